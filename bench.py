@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the masked-semiring hot path on one GB300 (replicas on N GPUs).
+
+Workload (one step): the undirected R-MAT scale-22 graph (edge factor 16, a/b/c = .57/.19/.19,
+seed 20210404, symmetrised, deduplicated; the stand-in for the paper's Kron graph), resident in
+HBM as int32 CSR.  A step runs the whole path on it through the C ABI:
+  graph store (new graph, degrees, the degree-ordered orientation U of Alg. 6),
+  triangle count (masked SpGEMM C<s(L)> = L plus.pair U' fused with its reduction),
+  direction-optimizing parents BFS from 16 seeded non-isolated sources (Alg. 2),
+  PageRank (Alg. 3, damping 0.85, tol 1e-7, at most 100 iterations, float32),
+and frees the cached properties, so every step rebuilds them.
+
+value = traversed edges per second over the whole step (GTEPS): the triangle count contributes
+the m/2 undirected edges, each BFS the undirected edges of its source's component (the Graph500
+convention), each PageRank iteration the m/2 undirected edges.  The CSR (537 MB) is larger than
+the 129 MB L2, so no extra flush is done between steps.
+
+--impl reference times the CPU oracle (single thread, float64, Alg. 6 / Alg. 1 / Alg. 3) on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TC/BFS GTEPS, PageRank iter GB/s vs ~8 TB/s HBM; batched & adjoint vs plain"
+SCALE, EF, NSRC, SEED = 22, 16, 16, 20210404
+DAMPING, TOL, ITERMAX = 0.85, 1e-7, 100
+WORKLOAD = f"rmat{SCALE}_ef{EF}: tc(auto sort) + do-bfs x{NSRC} + pagerank(0.85, tol 1e-7)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# replicas on N GPUs: one process per GPU, no data-path collective; only the timing is reduced
+# ---------------------------------------------------------------------------------------------
+
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's time (host-side gloo all-reduce; identity for one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes the same units per step (weak scaling)."""
+    return units_per_rank * world / (ms_per_step * 1e-3)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2104_01661_gb300 as L
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L.load_library()
+
+    g = gen.rmat(SCALE, EF, seed=SEED)
+    srcs = [int(s) for s in gen.sources(g, NSRC, seed=SEED)]
+    n, nnz = g.n, g.nnz
+    m_und = nnz // 2
+    rp_h = torch.from_numpy(g.rowptr).pin_memory()
+    ci_h = torch.from_numpy(g.colidx).pin_memory()
+    rp = rp_h.to(dev)
+    ci = ci_h.to(dev)
+    level = torch.empty((NSRC, n), dtype=torch.int32, device=dev)
+    parent = torch.empty((NSRC, n), dtype=torch.int32, device=dev)
+    rank_v = torch.empty(n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(rowptr, colidx, marks=None):
+        G = L.Graph(rowptr, colidx)
+        if marks is not None:
+            marks[0].record(stream)
+        t = L.lagr_tc(G, L.LAGR_TC_AUTO)
+        if marks is not None:
+            marks[1].record(stream)
+        for i, s in enumerate(srcs):
+            L.lagr_bfs(G, s, 0, level=level[i], parent=parent[i])
+        if marks is not None:
+            marks[2].record(stream)
+        _, iters = L.lagr_pagerank(G, DAMPING, TOL, ITERMAX, rank=rank_v)
+        if marks is not None:
+            marks[3].record(stream)
+        G.free()
+        return t, iters
+
+    # first run: results and the per-source component sizes for GTEPS
+    t_tri, iters = step(rp, ci)
+    torch.cuda.synchronize()
+    deg = torch.from_numpy(np.diff(g.rowptr).astype(np.int64)).to(dev)
+    comp_edges = [int(deg[level[i] >= 0].sum().item()) // 2 for i in range(NSRC)]
+    edges_per_step = m_und + sum(comp_edges) + iters * m_und
+
+    for _ in range(args.warmup):
+        step(rp, ci)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    marks = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    start, end = ev(), ev()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        start.record(stream)
+        for k in range(args.steps):
+            step(rp, ci, marks[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+    ms_total = max_over_ranks(start.elapsed_time(end), world)
+    ms_step = ms_total / args.steps
+    tc_ms = statistics.median(m[0].elapsed_time(m[1]) for m in marks)
+    bfs_ms = statistics.median(m[1].elapsed_time(m[2]) for m in marks)
+    pr_ms = statistics.median(m[2].elapsed_time(m[3]) for m in marks)
+
+    # end to end through the public API with host buffers: H2D of the CSR, the step, D2H results
+    h2d = rp_h.numel() * 4 + ci_h.numel() * 4
+    lvl_h = torch.empty((NSRC, n), dtype=torch.int32).pin_memory()
+    par_h = torch.empty((NSRC, n), dtype=torch.int32).pin_memory()
+    rank_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    d2h = lvl_h.numel() * 4 + par_h.numel() * 4 + rank_h.numel() * 4 + 8
+    e_start, e_end = ev(), ev()
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    for _ in range(args.steps):
+        rp_d = rp_h.to(dev, non_blocking=True)
+        ci_d = ci_h.to(dev, non_blocking=True)
+        step(rp_d, ci_d)
+        lvl_h.copy_(level, non_blocking=True)
+        par_h.copy_(parent, non_blocking=True)
+        rank_h.copy_(rank_v, non_blocking=True)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), world) / args.steps
+
+    # roofline of the PageRank iteration kernel and the triangle pass, from the live timings
+    hbm_peak, peak_kind = peaks()
+    pr_bytes_iter = 4 * (n + 1) + 4 * nnz + 20 * n
+    pr_gbs = pr_bytes_iter * iters / (pr_ms * 1e-3) / 1e9
+
+    # our kernels per step, counted once with the CUDA profiler outside the timed region
+    launches = count_launches(lambda: step(rp, ci))
+
+    out = None
+    if rank == 0:
+        clocks = clk.summary()
+        gteps = job_throughput(edges_per_step, world, ms_step) / 1e9
+        out = {
+            "metric": METRIC,
+            "value": round(gteps, 4),
+            "unit": "GTEPS",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int32 (TC uint64, BFS int32), f32 (PageRank)",
+            "data": "synthetic (seeded R-MAT, stand-in for the paper's Kron graph)",
+            "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "sources": NSRC,
+                       "l2": "inputs larger than L2 (CSR 537 MB > 129 MB); no extra flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clocks,
+            "e2e": {"value": round(job_throughput(edges_per_step, world, e2e_ms) / 1e9, 4), "unit": "GTEPS",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches * args.steps if launches is not None else None,
+            "components": {
+                "triangles": t_tri, "tc_ms": round(tc_ms, 3), "tc_mteps": round(m_und / (tc_ms * 1e-3) / 1e6, 1),
+                "bfs_ms_16_sources": round(bfs_ms, 3),
+                "bfs_gteps": round(sum(comp_edges) / (bfs_ms * 1e-3) / 1e9, 3),
+                "pagerank_ms": round(pr_ms, 3), "pagerank_iters": iters,
+                "pagerank_gbs_algorithmic": round(pr_gbs, 1),
+            },
+        }
+        out["roofline"] = roofline(args, n, nnz, iters, pr_ms, hbm_peak, peak_kind)
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(g, srcs, budget_s=args.cpu_budget)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def roofline(args, n, nnz, iters, pr_ms, peak, peak_kind):
+    """Dominant HBM-bound kernel of the step: the PageRank gather iteration.  achieved =
+    algorithmic bytes per iteration / its mean duration (CUDA events around the PageRank call,
+    divided by the iterations run, so launch gaps count against it)."""
+    bytes_iter = 4 * (n + 1) + 4 * nnz + 20 * n
+    ach = bytes_iter * iters / (pr_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "pr_rows_rmat22.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    return {"kernel": "pr_rows (PageRank gather iteration)", "bound": "hbm", "achieved": round(ach, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "peak_kind": peak_kind,
+            "bytes_per_launch": bytes_iter, "traffic": traffic}
+
+
+def count_launches(fn):
+    """Kernels from liblagr launched by one call of fn, by the CUDA profiler (not timed)."""
+    try:
+        import torch
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+        ours = [nm for nm in names if "lagr" in nm]
+        return len(ours) if ours else None
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------------------------
+
+def cpu_sample(g, srcs, budget_s=20.0):
+    """A bounded sample of the workload on the oracle (single thread): BFS from the first source,
+    PageRank iterations (float64, Alg. 3), and Alg. 6 on every k-th mask row of L."""
+    import numpy as np
+
+    import oracle
+    edges = 0
+    secs = 0.0
+    t0 = time.perf_counter()
+    level, _, _ = oracle.bfs(g, srcs[0])
+    secs += time.perf_counter() - t0
+    deg = np.diff(g.rowptr)
+    edges += int(deg[level >= 0].sum()) // 2
+    t0 = time.perf_counter()
+    _, k, _ = oracle.pagerank(g, DAMPING, 0.0, 2)
+    secs += time.perf_counter() - t0
+    edges += k * (g.nnz // 2)
+    stride = max(1, int(os.environ.get("LAGR_ORACLE_TC_STRIDE", "4096")))
+    _, ent, tsec = oracle.tc_sample(g, 0, stride)
+    secs += tsec
+    edges += ent
+    sample = (f"oracle on the same graph: BFS from source {srcs[0]}, 2 PageRank iterations, Alg. 6 on "
+              f"every {stride}-th mask row of L ({ent} mask entries; sort/split setup not timed)")
+    return edges, secs, sample
+
+
+def cpu_baseline(g, srcs, budget_s=20.0):
+    edges, secs, sample = cpu_sample(g, srcs, budget_s)
+    return {"value": round(edges / secs / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": sample, "seconds": round(secs, 2)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import gen
+    g = gen.rmat(SCALE, EF, seed=SEED)
+    srcs = [int(s) for s in gen.sources(g, NSRC, seed=SEED)]
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not repeated on the CPU
+    edges = 0
+    secs = 0.0
+    sample = ""
+    for _ in range(args.steps):
+        e, s, sample = cpu_sample(g, srcs)
+        edges += e
+        secs += s
+    v = edges / secs / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "GTEPS",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(secs / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 / int32 (oracle)", "data": "synthetic (seeded R-MAT)",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": round(v, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    out = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,286 @@
+/*
+ * lagr.h -- C ABI of the GB300 masked-semiring graph library.
+ *
+ * The library computes the data-parallel products under LAGraph's algorithms
+ * (Mattson et al., 2021) on one GPU:
+ *   - triangle counting, C<s(L)> = L plus.pair U' followed by a reduction
+ *     (Alg. 6, Sec. IV-F), fused so that C is never materialised;
+ *   - direction-optimizing parents BFS, push q'A / pull A'q over any.secondi
+ *     with the visited set as a complemented structural mask (Alg. 1 and 2,
+ *     Sec. IV-A);
+ *   - PageRank, repeated A' plus.second w (Alg. 3, Sec. IV-C), a weighted
+ *     plus.times form and its adjoint;
+ *   - batched forms: 64 BFS sources in one bitmap frontier (the ns x n
+ *     frontier of Alg. 4, Sec. IV-B) and many graphs in one launch.
+ *
+ * Conventions (Sec. II-D, II-E):
+ *   - arguments are ordered outputs, then input/outputs, then inputs, then
+ *     `msg`;
+ *   - the return value is 0 on success, < 0 on error, > 0 for a warning;
+ *   - `msg` is a caller-owned buffer of LAGR_MSG_LEN chars (or NULL).  It is
+ *     set to "" on success and holds a description on an error or warning;
+ *   - an output that is not wanted may be passed as NULL.
+ *
+ * Memory: every array argument documented "device" is a device pointer that
+ * the caller allocates and keeps alive for the duration of the call (and, for
+ * the graph's primary arrays, for the life of the graph).  Work space and
+ * cached graph properties are allocated by the library through the allocator
+ * set with lagr_set_allocator (stream-ordered cudaMallocAsync by default).
+ *
+ * Streams: every call takes a CUDA stream as `void *stream` (a cudaStream_t;
+ * NULL means the legacy default stream) and issues all its device work on
+ * it.  Calls that return a host scalar (lagr_tc's count, lagr_pagerank's
+ * iteration count, lagr_bfs's depth) synchronise that stream before they
+ * return; the others return once the work is enqueued, except where noted.
+ *
+ * Index types: int32 vertex ids and row pointers, so n < 2^31 and
+ * nnz < 2^31 (larger inputs are rejected with LAGR_ERR_TOO_LARGE).
+ */
+#ifndef LAGR_H
+#define LAGR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LAGR_MSG_LEN 256
+
+/* return codes (Sec. II-D: 0 ok, < 0 error, > 0 warning) */
+#define LAGR_OK 0
+#define LAGR_ERR_NULL_POINTER (-1)
+#define LAGR_ERR_INVALID_VALUE (-2)
+#define LAGR_ERR_INVALID_GRAPH (-3)
+#define LAGR_ERR_PROPERTY_MISSING (-4)
+#define LAGR_ERR_OUT_OF_MEMORY (-5)
+#define LAGR_ERR_CUDA (-6)
+#define LAGR_ERR_TIMEOUT (-7)
+#define LAGR_ERR_DEVICE_CHECK (-8)
+#define LAGR_ERR_TOO_LARGE (-9)
+#define LAGR_WARN_NOT_CONVERGED 1
+
+/* graph kinds (Sec. II-A) */
+#define LAGR_UNDIRECTED 0
+#define LAGR_DIRECTED 1
+
+/* lagr_tc methods: the degree-sort decision of Alg. 6 */
+#define LAGR_TC_AUTO 0   /* sort when mean degree > 4 x median degree, as Alg. 6 */
+#define LAGR_TC_SORT 1   /* always orient by ascending degree */
+#define LAGR_TC_NOSORT 2 /* never: L = tril(A,-1), U = triu(A,1) on the given labels */
+
+/* lagr_bfs flags */
+#define LAGR_BFS_PUSH_ONLY 1 /* Alg. 1: every level is a push q'A */
+#define LAGR_BFS_PULL_ONLY 2 /* every level after the first is a pull A'q */
+
+/* lagr_pagerank / lagr_pagerank_backward flags */
+#define LAGR_PR_GAP 0            /* Alg. 3 as written: dangling rows lose their mass */
+#define LAGR_PR_DANGLING 1       /* redistribute the dangling mass through the teleport vector */
+#define LAGR_PR_WEIGHTED 2       /* plus.times with the graph's values (row-stochastic W) */
+#define LAGR_PR_WARM_START 4     /* `rank` holds the starting vector on entry */
+
+/*
+ * The graph (Sec. II-A): primary components plus cached properties.  The
+ * struct is not opaque; a field that is not known is NULL (or -1 for the
+ * scalars).  The primary arrays are BORROWED device pointers: the caller
+ * keeps ownership and must keep them alive and unchanged while the graph
+ * exists (if they change, call lagr_delete_properties).  Cached properties
+ * are owned by the library and freed by lagr_delete_properties /
+ * lagr_graph_free.
+ */
+typedef struct lagr_graph_struct {
+  /* primary components */
+  int32_t n;             /* number of vertices */
+  int64_t nnz;           /* number of stored entries of A */
+  int32_t kind;          /* LAGR_UNDIRECTED (A symmetric) or LAGR_DIRECTED */
+  const int32_t *rowptr; /* device [n+1], rowptr[0] = 0, nondecreasing, rowptr[n] = nnz */
+  const int32_t *colidx; /* device [nnz], each row strictly increasing, 0 <= j < n */
+  const float *val;      /* device [nnz] or NULL: edge values (used by LAGR_PR_WEIGHTED) */
+
+  /* cached: A' held by row (the CSC of A).  For an undirected graph these
+   * alias the primary arrays. */
+  int32_t *at_rowptr, *at_colidx;
+  float *at_val;
+  int32_t at_owned;
+
+  /* cached: degrees (row degree of A; the column degree is that of A') */
+  int32_t *row_degree;
+
+  /* cached: triangle-counting orientation U (strict upper part after the
+   * optional degree ordering of Alg. 6), held by row, with the original
+   * vertex labels; u_order is the LAGR_TC_* method it was built for. */
+  int32_t *u_rowptr, *u_colidx;
+  int64_t u_nnz;
+  int32_t u_order;
+
+  /* cached scalars */
+  int32_t a_pattern_is_symmetric; /* -1 unknown, 0 no, 1 yes */
+  int64_t ndiag;                  /* number of self-loops, -1 unknown */
+
+  /* statistics of the last call on this graph */
+  int32_t last_levels;      /* BFS: number of levels (depth) */
+  int32_t last_push_levels; /* BFS: levels done as push */
+  int32_t last_pull_levels; /* BFS: levels done as pull */
+  int32_t last_iters;       /* PageRank: iterations done */
+  double last_resid;        /* PageRank: last L1 change */
+
+  void *priv; /* library-private work space; do not touch */
+} lagr_graph_struct;
+
+typedef lagr_graph_struct *lagr_graph;
+
+/*
+ * Allocator hook (Sec. IV, the malloc/free wrappers): every device
+ * allocation of the library goes through alloc(bytes, stream, ctx) and
+ * free_(ptr, stream, ctx).  alloc returns NULL on failure, which the calling
+ * function reports as LAGR_ERR_OUT_OF_MEMORY.  Passing NULLs restores the
+ * default (cudaMallocAsync / cudaFreeAsync on the call's stream).  Not
+ * thread-safe: set it before the first call.
+ */
+typedef void *(*lagr_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*lagr_free_fn)(void *ptr, void *stream, void *ctx);
+int lagr_set_allocator(lagr_alloc_fn alloc, lagr_free_fn free_, void *ctx);
+
+/*
+ * Create a graph from a device CSR (the "move" constructor of Sec. II-A,
+ * except that the arrays are borrowed, not moved: PyTorch or the caller owns
+ * device memory).  Host-only: no device work, no validation beyond sizes
+ * (see lagr_graph_check).  *G receives a new host struct.
+ * Errors: NULL_POINTER (G, or rowptr/colidx with n > 0 / nnz > 0),
+ * INVALID_VALUE (n < 0, nnz < 0, bad kind), TOO_LARGE (n or nnz >= 2^31).
+ */
+int lagr_graph_new(lagr_graph *G, int32_t n, int64_t nnz, const int32_t *rowptr,
+                   const int32_t *colidx, const float *val, int32_t kind, char *msg);
+
+/* Free the struct and every cached property; *G is set to NULL.  Frees are
+ * issued on `stream`.  A NULL *G is a no-op. */
+int lagr_graph_free(lagr_graph *G, void *stream, char *msg);
+
+/* Drop every cached property (Sec. IV, DeleteProperties). */
+int lagr_delete_properties(lagr_graph G, void *stream, char *msg);
+
+/*
+ * Validate the graph on the device (Sec. IV, CheckGraph): rowptr[0] = 0,
+ * rowptr nondecreasing, rowptr[n] = nnz, every column index in [0, n), each
+ * row strictly increasing (sorted, no duplicates), and, for
+ * LAGR_UNDIRECTED, A equal to A'.  Sets a_pattern_is_symmetric and ndiag.
+ * Returns LAGR_ERR_INVALID_GRAPH with a description when a check fails.
+ * Synchronises the stream.
+ */
+int lagr_graph_check(lagr_graph G, void *stream, char *msg);
+
+/* Compute and cache A' by row (Sec. II-A, Property_AT).  Rows of A' are
+ * sorted; for an undirected graph A' aliases A.  Deterministic. */
+int lagr_property_AT(lagr_graph G, void *stream, char *msg);
+
+/* Compute and cache the row degree (Sec. IV, Property_RowDegree). */
+int lagr_property_row_degree(lagr_graph G, void *stream, char *msg);
+
+/*
+ * Triangle count (Alg. 6, Sec. IV-F): the number of unique 3-cliques of the
+ * undirected graph G, i.e. t = sum(C) with C<s(L)> = L plus.pair U', L and U
+ * the strictly lower and upper parts of A after the degree ordering that
+ * `method` selects (LAGR_TC_*).  Self-loops are ignored (strict parts).
+ * The product C is never formed; the count is exact (uint64).
+ * ntriangles: host, output.  Caches G->u_* (the orientation).  Synchronises
+ * the stream.  Errors: NULL_POINTER, INVALID_VALUE (bad method),
+ * INVALID_GRAPH (G directed), OUT_OF_MEMORY, CUDA.
+ */
+int lagr_tc(uint64_t *ntriangles, lagr_graph G, int32_t method, void *stream, char *msg);
+
+/*
+ * Parents BFS (Alg. 1 / Alg. 2, Sec. IV-A).  level[v] = number of edges on a
+ * shortest path from src to v (-1 when unreachable); parent[v] = some u with
+ * A(u,v) stored and level[u] = level[v] - 1 (the `any` monoid: which one is
+ * unspecified), parent[src] = src, -1 when unreachable.  Direction
+ * optimisation switches between push (rows of A) and pull (rows of A') per
+ * level; flags may force one direction.  Directed graphs follow out-edges;
+ * the pull needs A' (computed and cached when missing).
+ * level, parent: device [n] outputs, either may be NULL.  depth: host output
+ * (number of levels, >= 1) or NULL.  Synchronises the stream.
+ * Errors: NULL_POINTER, INVALID_VALUE (src out of range, bad flags),
+ * OUT_OF_MEMORY, TIMEOUT (a capped device wait ran out), CUDA.
+ */
+int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G, int32_t src,
+             int32_t flags, void *stream, char *msg);
+
+/*
+ * k BFS at once (1 <= k <= 64) from the sources src[0..k-1] (host array),
+ * as one 64-bit bitmap frontier per vertex: the frontier matrix of Alg. 4
+ * (Sec. IV-B) with ns = k and the any/or monoid in place of plus.
+ * level: device [k][n] output, row s holds the levels from src[s] with the
+ * same meaning as lagr_bfs.  Undirected graphs only.  Synchronises the
+ * stream.  Errors: NULL_POINTER, INVALID_VALUE (k out of range or a source
+ * out of range), INVALID_GRAPH (directed), OUT_OF_MEMORY, CUDA.
+ */
+int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src, int32_t k, void *stream,
+                     char *msg);
+
+/*
+ * PageRank (Alg. 3, Sec. IV-C) in float32.
+ * Unweighted (flags without LAGR_PR_WEIGHTED):
+ *   r = 1/n; repeat: t = r; w = damping * t / d_out (rows with d_out > 0);
+ *   r = (1 - damping) * v + A' plus.second w [+ damping * (sum of t over
+ *   dangling rows) * v when LAGR_PR_DANGLING]; stop when sum|t - r| < tol.
+ * Weighted (LAGR_PR_WEIGHTED; G->val holds a row-stochastic W):
+ *   r = (1 - damping) v + damping W' r [+ dangling term as above].
+ * v is `teleport` (device [n], a distribution) or uniform 1/n when NULL.
+ * rank: device [n] output (input too with LAGR_PR_WARM_START).  iters: host
+ * output or NULL.  Returns LAGR_WARN_NOT_CONVERGED when itermax iterations
+ * did not reach tol (rank holds the last iterate).  Synchronises the stream.
+ * Errors: NULL_POINTER, INVALID_VALUE (damping outside (0,1), itermax < 1,
+ * tol < 0, WEIGHTED without values), OUT_OF_MEMORY, CUDA.
+ */
+int lagr_pagerank(float *rank, int32_t *iters, lagr_graph G, float damping, float tol,
+                  int32_t itermax, const float *teleport, int32_t flags, void *stream, char *msg);
+
+/*
+ * Adjoint of the weighted PageRank fixed point (the paper has no adjoint;
+ * this is the implicit-function derivative of the iteration above).  For a
+ * loss L with dL/drank = g, solve
+ *   lambda = g + damping W lambda [+ damping (v . lambda) 1_dangling]
+ * by the same gather machinery on the rows of W, then
+ *   dL/dW(i,j) = damping * rank(i) * lambda(j)      (every stored (i,j))
+ *   dL/dv(j)   = ((1 - damping) + damping * delta) * lambda(j),
+ * delta = sum of rank over dangling rows under LAGR_PR_DANGLING, else 0.
+ * rank: device [n], the forward fixed point, or NULL to recompute it here
+ * (nothing is stored per iteration either way).  dL_dw: device [nnz] output
+ * in CSR order, or NULL.  dL_dteleport: device [n] output or NULL.
+ * iters: host output (adjoint iterations) or NULL.  Uses G->val (W);
+ * flags must include LAGR_PR_WEIGHTED.  Synchronises the stream.
+ */
+int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t *iters,
+                           const float *dL_drank, const float *rank, lagr_graph G, float damping,
+                           float tol, int32_t itermax, const float *teleport, int32_t flags,
+                           void *stream, char *msg);
+
+/*
+ * Many graphs at once.  A batch is g undirected graphs concatenated
+ * block-diagonally into one CSR (vertex ids shifted by voff).  A plan holds
+ * the orientation, the work partition and a CUDA graph of the whole pass
+ * (triangle count of every member, then `iters` PageRank iterations, GAP
+ * form, of every member, the teleport of member i being (1-damping)/n_i);
+ * lagr_batch_run replays it as one graph launch.
+ * lagr_batch_plan: voff is a HOST array [g+1]; rowptr/colidx device arrays of
+ * the concatenated CSR, borrowed for the plan's life.  tile: rows per work
+ * item of the triangle kernel (0 = autotune; the choice is cached in
+ * tune_cache, a JSON file path, when not NULL).
+ * lagr_batch_run: ntri device [g] (uint64), rank device [N] (float).
+ */
+typedef struct lagr_batch_struct *lagr_batch;
+int lagr_batch_plan(lagr_batch *B, int32_t g, const int32_t *voff, int32_t N, int64_t nnz,
+                    const int32_t *rowptr, const int32_t *colidx, float damping, int32_t iters,
+                    int32_t tile, const char *tune_cache, void *stream, char *msg);
+int lagr_batch_run(uint64_t *ntri, float *rank, lagr_batch B, void *stream, char *msg);
+int lagr_batch_tile(int32_t *tile, lagr_batch B);
+int lagr_batch_free(lagr_batch *B, void *stream, char *msg);
+
+/* library version string */
+const char *lagr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAGR_H */

@@ -47,6 +47,9 @@ def _load():
         f64p = ctypes.POINTER(ctypes.c_double)
         lib.oracle_tc.argtypes = [i32, i32p, i32p, ctypes.c_int]
         lib.oracle_tc.restype = ctypes.c_uint64
+        lib.oracle_tc_sample.argtypes = [i32, i32p, i32p, ctypes.c_int, i32, ctypes.POINTER(ctypes.c_int64),
+                                         f64p]
+        lib.oracle_tc_sample.restype = ctypes.c_uint64
         lib.oracle_tc_wants_sort.argtypes = [i32, i32p, f64p, ctypes.POINTER(ctypes.c_int64)]
         lib.oracle_tc_wants_sort.restype = ctypes.c_int
         lib.oracle_bfs.argtypes = [i32, i32p, i32p, i32, i32p, i32p]
@@ -90,6 +93,18 @@ def tc(g, method: int = TC_AUTO) -> int:
     if t == 2**64 - 1:
         raise MemoryError("oracle_tc")
     return int(t)
+
+
+def tc_sample(g, method: int = TC_AUTO, stride: int = 1):
+    """Alg. 6 restricted to mask rows 0, stride, 2*stride, ... of L: (partial count, mask entries
+    visited, seconds spent in the masked product)."""
+    n, rp, prp, ci, pci = _csr(g)
+    ent = ctypes.c_int64()
+    sec = ctypes.c_double()
+    t = _load().oracle_tc_sample(n, prp, pci, method, stride, ctypes.byref(ent), ctypes.byref(sec))
+    if t == 2**64 - 1:
+        raise MemoryError("oracle_tc_sample")
+    return int(t), int(ent.value), float(sec.value)
 
 
 def tc_wants_sort(g):

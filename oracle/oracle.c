@@ -32,10 +32,12 @@
  * column indices, rows sorted, no duplicates) as emitted by the seeded
  * generators.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <time.h>
 
 /* ------------------------------------------------------------------------- */
 /* small helpers                                                             */
@@ -87,8 +89,29 @@ int oracle_tc_wants_sort(int32_t n, const int32_t *rowptr, double *mean_out, int
  * 2 = never sort.  Returns the number of triangles, or UINT64_MAX on an
  * allocation failure.
  */
+uint64_t oracle_tc_sample(int32_t n, const int32_t *rowptr, const int32_t *colidx, int method, int32_t stride,
+                          int64_t *l_entries, double *count_seconds);
+
 uint64_t oracle_tc(int32_t n, const int32_t *rowptr, const int32_t *colidx, int method) {
+  return oracle_tc_sample(n, rowptr, colidx, method, 1, NULL, NULL);
+}
+
+static double now_seconds(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/*
+ * The same computation restricted to the mask rows i = 0, stride, 2*stride, ... of L (in the
+ * possibly degree-sorted labelling): a bounded sample of the work for timing.  stride = 1 is the
+ * whole count.  *l_entries receives the number of mask entries (i,j) visited and *count_seconds
+ * the time of the masked product alone (either may be NULL).
+ */
+uint64_t oracle_tc_sample(int32_t n, const int32_t *rowptr, const int32_t *colidx, int method, int32_t stride,
+                          int64_t *l_entries, double *count_seconds) {
   int64_t nnz = rowptr[n];
+  if (stride < 1) stride = 1;
   int sort = (method == 1) || (method == 0 && oracle_tc_wants_sort(n, rowptr, NULL, NULL));
 
   /* A = A(p,p) when sorting: new vertex i is old vertex p[i]. */
@@ -139,7 +162,10 @@ uint64_t oracle_tc(int32_t n, const int32_t *rowptr, const int32_t *colidx, int 
    * a merge of row i of L with row j of U.  Then t = sum over C.
    */
   uint64_t t = 0;
-  for (int32_t i = 0; i < n; i++) {
+  int64_t visited = 0;
+  double t0 = now_seconds();
+  for (int32_t i = 0; i < n; i += stride) {
+    visited += Lp[i + 1] - Lp[i];
     for (int32_t q = Lp[i]; q < Lp[i + 1]; q++) {
       int32_t j = Li[q];
       int32_t a = Lp[i], ae = Lp[i + 1], b = Up[j], be = Up[j + 1];
@@ -152,6 +178,8 @@ uint64_t oracle_tc(int32_t n, const int32_t *rowptr, const int32_t *colidx, int 
       t += cij;
     }
   }
+  if (count_seconds) *count_seconds = now_seconds() - t0;
+  if (l_entries) *l_entries = visited;
   free(Ap); free(Ai); free(Lp); free(Up); free(Li); free(Ui);
   return t;
 }

@@ -1,0 +1,543 @@
+// Parents BFS (Alg. 1 and Alg. 2, Sec. IV-A) and the 64-source bitmap BFS (the ns x n frontier
+// of Alg. 4, Sec. IV-B, with ns <= 64).
+//
+// One level is q'<!s(p),r> = q' any.secondi A (push) or q<!s(p),r> = A' any.secondi q (pull),
+// followed by p<s(q)> = q.  Here the two are fused: the kernel that discovers v writes parent[v]
+// (the secondi value: the frontier vertex that reached v; `any` keeps whichever claims v first)
+// and level[v] directly.  The complemented structural mask !s(p) is a visited bitmap; the
+// frontier is a vertex queue for push and a bitmap for pull (the bitmap format of Sec. V-A).
+//
+// Push expands 32 frontier vertices per warp with the load-balanced segment walk and claims
+// unvisited vertices with atomicOr on the visited bitmap.  Pull gives each unvisited vertex one
+// lane that scans its in-neighbours and stops at the first one in the frontier (any monoid).
+// Narrow frontiers (the high-diameter regime of the paper's road graph) run many levels inside
+// one single-CTA launch with only __syncthreads between levels.  The push/pull choice is
+// Beamer's rule: pull when the frontier's edges exceed the unexplored edges / alpha, push again
+// when the frontier shrinks below n / beta.
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace lagr {
+namespace {
+
+constexpr int BFS_THREADS = 256;
+constexpr int SMALL_THREADS = 1024;
+constexpr int64_t SMALL_MAX = 8192;  // frontiers up to this size stay in the single-CTA kernel
+constexpr int ALPHA_DO = 14;
+constexpr int BETA_DO = 24;
+
+// counters of one BFS call (device int64, mirrored to pinned host memory)
+enum BfsSlot {
+  B_NQ = 0,      // size of the current frontier
+  B_LEV = 1,     // last completed level
+  B_PAR = 2,     // which queue buffer holds the frontier (0: qa, 1: qb)
+  B_MU = 3,      // unexplored edges
+  B_MF = 4,      // edges out of the current frontier
+  B_NEXT = 5,    // next-frontier size being built
+  B_MNEXT = 6,   // edges out of the next frontier being built
+  B_EXIT = 7,    // why the single-CTA kernel returned
+  B_NSLOT = 8
+};
+
+__global__ void bfs_init(int32_t n, int32_t *__restrict__ level, int32_t *__restrict__ parent,
+                         uint32_t *__restrict__ visited, int64_t nwords) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (level) level[i] = -1;
+    if (parent) parent[i] = -1;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += stride) visited[i] = 0;
+}
+
+__global__ void bfs_seed(const int32_t *__restrict__ rowptr, int64_t nnz, int32_t src, int32_t *__restrict__ level,
+                         int32_t *__restrict__ parent, uint32_t *__restrict__ visited, int32_t *__restrict__ qa,
+                         int64_t *__restrict__ c) {
+  if (level) level[src] = 0;
+  if (parent) parent[src] = src;
+  visited[src >> 5] |= 1u << (src & 31);
+  qa[0] = src;
+  const int64_t d = rowptr[src + 1] - rowptr[src];
+  for (int i = 0; i < B_NSLOT; i++) c[i] = 0;
+  c[B_NQ] = 1;
+  c[B_MF] = d;
+  c[B_MU] = nnz - d;
+}
+
+// Claim v for the frontier vertex u at level lev.  Returns true when this thread won v.
+__device__ __forceinline__ bool claim(uint32_t *__restrict__ visited, int32_t v) {
+  const uint32_t bit = 1u << (v & 31);
+  if (visited[v >> 5] & bit) return false;
+  return !(atomicOr(&visited[v >> 5], bit) & bit);
+}
+
+// One push level over the frontier qin[0..nq): warps take 32 frontier vertices at a time.
+// Appends to qout through *qcount; adds the out-degree of every discovered vertex to *mcount.
+__device__ __forceinline__ void push_level(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                           const int32_t *__restrict__ qin, int64_t nq, int32_t *__restrict__ qout,
+                                           uint32_t *__restrict__ visited, int32_t *__restrict__ level,
+                                           int32_t *__restrict__ parent, int32_t lev, int64_t warp0, int64_t nwarps,
+                                           unsigned long long *qcount, unsigned long long &mdeg) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  for (int64_t wb = warp0 * 32; wb < nq; wb += nwarps * 32) {
+    const int64_t i = wb + lane;
+    int32_t u = -1, st = 0, len = 0;
+    if (i < nq) {
+      u = qin[i];
+      st = rowptr[u];
+      len = rowptr[u + 1] - st;
+    }
+    warp_segments(st, len, u, [&](bool valid, int uu, int, int gidx) {
+      bool won = false;
+      int32_t v = 0;
+      if (valid) {
+        v = colidx[gidx];
+        won = claim(visited, v);
+      }
+      const unsigned m = __ballot_sync(LAGR_FULL_MASK, won);
+      if (m) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(qcount, (unsigned long long)__popc(m));
+        pos = __shfl_sync(LAGR_FULL_MASK, pos, 0);
+        if (won) {
+          qout[pos + __popc(m & lt)] = v;
+          if (level) level[v] = lev;
+          if (parent) parent[v] = uu;
+          mdeg += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+        }
+      }
+    });
+  }
+}
+
+__global__ void __launch_bounds__(BFS_THREADS)
+    bfs_push(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
+             int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
+             int32_t *__restrict__ parent, int64_t *__restrict__ c) {
+  const int64_t nq = c[B_NQ];
+  const int32_t lev = (int32_t)c[B_LEV] + 1;
+  const int par = (int)c[B_PAR];
+  const int32_t *qin = par ? qb : qa;
+  int32_t *qout = par ? qa : qb;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long mdeg = 0;
+  push_level(rowptr, colidx, qin, nq, qout, visited, level, parent, lev, warp0, nwarps,
+                    (unsigned long long *)&c[B_NEXT], mdeg);
+  mdeg = warp_sum(mdeg);
+  if ((threadIdx.x & 31) == 0 && mdeg) atomicAdd((unsigned long long *)&c[B_MNEXT], mdeg);
+}
+
+// Many narrow push levels in one CTA.  Returns when the frontier is empty, grows past SMALL_MAX,
+// the direction rule asks for a pull, or max_level is reached.
+__global__ void __launch_bounds__(SMALL_THREADS)
+    bfs_push_small(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
+                   int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
+                   int32_t *__restrict__ parent, int64_t *__restrict__ c, int32_t max_level, int allow_pull) {
+  __shared__ unsigned long long s_next, s_mdeg;
+  int64_t nq = c[B_NQ], mu = c[B_MU], mf = c[B_MF];
+  int32_t lev = (int32_t)c[B_LEV];
+  int par = (int)c[B_PAR];
+  const int64_t warp0 = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int exit_reason = 0;
+  bool first = true, growing = false;
+  for (;;) {
+    if (nq == 0) { exit_reason = 1; break; }
+    if (nq > SMALL_MAX) { exit_reason = 2; break; }
+    // the caller chose push for the first level; afterwards pull when a growing frontier's
+    // edges outweigh the unexplored edges / alpha
+    if (!first && allow_pull && growing && mf > mu / ALPHA_DO) { exit_reason = 3; break; }
+    if (lev + 1 > max_level) { exit_reason = 4; break; }
+    const int64_t nq_before = nq;
+    if (threadIdx.x == 0) {
+      s_next = 0;
+      s_mdeg = 0;
+    }
+    __syncthreads();
+    const int32_t *qin = par ? qb : qa;
+    int32_t *qout = par ? qa : qb;
+    unsigned long long mdeg = 0;
+    push_level(rowptr, colidx, qin, nq, qout, visited, level, parent, lev + 1, warp0, nwarps, &s_next, mdeg);
+    mdeg = warp_sum(mdeg);
+    if ((threadIdx.x & 31) == 0 && mdeg) atomicAdd(&s_mdeg, mdeg);
+    __syncthreads();
+    nq = (int64_t)s_next;
+    mf = (int64_t)s_mdeg;
+    mu -= mf;
+    lev += 1;
+    par ^= 1;
+    growing = nq > nq_before;
+    first = false;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    c[B_NQ] = nq;
+    c[B_LEV] = lev;
+    c[B_PAR] = par;
+    c[B_MU] = mu;
+    c[B_MF] = mf;
+    c[B_EXIT] = exit_reason;
+  }
+}
+
+// queue -> frontier bitmap (the bitmap is cleared first by the caller)
+__global__ void bfs_q2b(const int32_t *__restrict__ qa, const int32_t *__restrict__ qb, const int64_t *__restrict__ c,
+                        uint32_t *__restrict__ fbits) {
+  const int64_t nq = c[B_NQ];
+  const int32_t *q = c[B_PAR] ? qb : qa;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = q[i];
+    atomicOr(&fbits[v >> 5], 1u << (v & 31));
+  }
+}
+
+// frontier bitmap -> queue qa (order of the words; B_PAR is reset to 0 by the host update)
+__global__ void bfs_b2q(const uint32_t *__restrict__ fbits, int64_t nwords, int32_t *__restrict__ qa,
+                        unsigned long long *__restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nwords; base += stride) {
+    const int64_t w = base + lane;
+    uint32_t word = (w < nwords) ? fbits[w] : 0u;
+    const int cnt = __popc(word);
+    const int incl = warp_inclusive_scan(cnt);
+    const int tot = __shfl_sync(LAGR_FULL_MASK, incl, 31);
+    unsigned long long p = 0;
+    if (lane == 31 && tot) p = atomicAdd(count, (unsigned long long)tot);
+    p = __shfl_sync(LAGR_FULL_MASK, p, 31);
+    int64_t pos = (int64_t)p + incl - cnt;
+    while (word) {
+      const int b = __ffs(word) - 1;
+      qa[pos++] = (int32_t)(w * 32 + b);
+      word &= word - 1;
+    }
+  }
+}
+
+// One pull level: each unvisited vertex scans its in-neighbours (rows of A') for one in the
+// frontier.  A warp owns one 32-vertex word of the bitmaps, so it updates them without atomics.
+__global__ void __launch_bounds__(BFS_THREADS)
+    bfs_pull(const int32_t *__restrict__ at_rowptr, const int32_t *__restrict__ at_colidx,
+             const int32_t *__restrict__ rowptr, int32_t n, const uint32_t *__restrict__ fbits,
+             uint32_t *__restrict__ nbits, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
+             int32_t *__restrict__ parent, int64_t *__restrict__ c) {
+  const int lane = threadIdx.x & 31;
+  const int32_t lev = (int32_t)c[B_LEV] + 1;
+  const int64_t nwords = ((int64_t)n + 31) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long found_n = 0, mdeg = 0;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords; w += warps) {
+    const uint32_t vis = visited[w];
+    const int64_t v = w * 32 + lane;
+    const bool need = v < n && !((vis >> lane) & 1u);
+    if (!__any_sync(LAGR_FULL_MASK, need)) {
+      if (lane == 0) nbits[w] = 0;
+      continue;
+    }
+    int32_t par = -1;
+    if (need) {
+      const int32_t b = at_rowptr[v], e = at_rowptr[v + 1];
+      for (int32_t k = b; k < e; k++) {
+        const int32_t u = at_colidx[k];
+        if ((fbits[u >> 5] >> (u & 31)) & 1u) {
+          par = u;
+          break;
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(LAGR_FULL_MASK, par >= 0);
+    if (lane == 0) {
+      nbits[w] = m;
+      if (m) visited[w] = vis | m;
+      found_n += __popc(m);
+    }
+    if (par >= 0) {
+      if (level) level[v] = lev;
+      if (parent) parent[v] = par;
+      mdeg += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+    }
+  }
+  found_n = warp_sum(found_n);
+  mdeg = warp_sum(mdeg);
+  if (lane == 0) {
+    if (found_n) atomicAdd((unsigned long long *)&c[B_NEXT], found_n);
+    if (mdeg) atomicAdd((unsigned long long *)&c[B_MNEXT], mdeg);
+  }
+}
+
+// after a level: the next frontier becomes the current one
+__global__ void bfs_advance(int64_t *__restrict__ c, int flip) {
+  c[B_NQ] = c[B_NEXT];
+  c[B_MF] = c[B_MNEXT];
+  c[B_MU] -= c[B_MNEXT];
+  c[B_LEV] += 1;
+  if (flip) c[B_PAR] ^= 1;
+  c[B_NEXT] = 0;
+  c[B_MNEXT] = 0;
+}
+
+__global__ void bfs_set_par(int64_t *__restrict__ c, int par) { c[B_PAR] = par; }
+
+inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// ---- 64 sources at once -------------------------------------------------------------------------
+
+__global__ void bfs64_init(int32_t n, int32_t k, int32_t *__restrict__ level, unsigned long long *__restrict__ seen,
+                           unsigned long long *__restrict__ front) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    seen[i] = 0;
+    front[i] = 0;
+  }
+  const int64_t total = (int64_t)k * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) level[i] = -1;
+}
+
+__global__ void bfs64_seed(int32_t n, int32_t k, const int32_t *__restrict__ src, int32_t *__restrict__ level,
+                           unsigned long long *__restrict__ seen, unsigned long long *__restrict__ front) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < k; s++) {
+      const int32_t v = src[s];
+      seen[v] |= 1ull << s;
+      front[v] |= 1ull << s;
+      level[(int64_t)s * n + v] = 0;
+    }
+  }
+}
+
+// next[v] = (OR over in-neighbours u of front[u]) & ~seen[v]; the any/or monoid stops the scan
+// as soon as every still-unseen source bit of v is covered.
+__global__ void __launch_bounds__(BFS_THREADS)
+    bfs64_pull(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t n, int32_t k,
+               unsigned long long kmask, const unsigned long long *__restrict__ front,
+               unsigned long long *__restrict__ next, unsigned long long *__restrict__ seen,
+               int32_t *__restrict__ level, int32_t lev, unsigned long long *__restrict__ newcount) {
+  unsigned long long found = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long sv = seen[v];
+    unsigned long long nw = 0;
+    if (sv != kmask) {
+      unsigned long long acc = 0;
+      const int32_t b = rowptr[v], e = rowptr[v + 1];
+      for (int32_t q = b; q < e; q++) {
+        acc |= __ldg(&front[colidx[q]]);
+        if ((acc | sv) == kmask) break;
+      }
+      nw = acc & ~sv;
+      if (nw) {
+        seen[v] = sv | nw;
+        found++;
+        unsigned long long bits = nw;
+        while (bits) {
+          const int s = __ffsll((long long)bits) - 1;
+          level[(int64_t)s * n + v] = lev;
+          bits &= bits - 1;
+        }
+      }
+    }
+    next[v] = nw;
+  }
+  found = warp_sum(found);
+  if ((threadIdx.x & 31) == 0 && found) atomicAdd(newcount, found);
+}
+
+}  // namespace
+}  // namespace lagr
+
+using namespace lagr;
+
+extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G, int32_t src, int32_t flags,
+                        void *stream, char *msg) {
+  LAGR_TRY(check_graph_arg(G, msg));
+  if (src < 0 || src >= G->n) {
+    set_msg(msg, "source %d out of range [0, %d)", src, G->n);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  if (flags & ~(LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY) ||
+      (flags & (LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY)) == (LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY)) {
+    set_msg(msg, "bad BFS flags 0x%x", flags);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Priv *P = nullptr;
+  LAGR_TRY(priv_get(G, s, msg, &P));
+  const bool push_only = flags & LAGR_BFS_PUSH_ONLY;
+  const bool pull_only = flags & LAGR_BFS_PULL_ONLY;
+  if (!push_only) LAGR_TRY(lagr_property_AT(G, s, msg));
+  const int32_t n = G->n;
+  const int64_t nwords = ((int64_t)n + 31) / 32;
+  Temp<uint32_t> visited(s), fbits(s), nbits(s);
+  Temp<int32_t> qa(s), qb(s);
+  Temp<int64_t> cnt(s);
+  LAGR_TRY(visited.alloc(nwords, msg, "visited bitmap"));
+  LAGR_TRY(fbits.alloc(nwords, msg, "frontier bitmap"));
+  LAGR_TRY(nbits.alloc(nwords, msg, "next frontier bitmap"));
+  LAGR_TRY(qa.alloc(n, msg, "frontier queue"));
+  LAGR_TRY(qb.alloc(n, msg, "frontier queue"));
+  LAGR_TRY(cnt.alloc(B_NSLOT, msg, "BFS counters"));
+  bfs_init<<<grid_for(n, 256), 256, 0, s>>>(n, level, parent, visited.p, nwords);
+  bfs_seed<<<1, 1, 0, s>>>(G->rowptr, G->nnz, src, level, parent, visited.p, qa.p, cnt.p);
+  LAGR_LAUNCH_CHECK();
+
+  int64_t *h = P->hscal;  // pinned mirror of the counters
+  auto sync_counters = [&]() -> int {
+    LAGR_CUDA_TRY(cudaMemcpyAsync(h, cnt.p, B_NSLOT * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+    return LAGR_OK;
+  };
+  // frontier representation: 0 = queue (push), 1 = bitmap fbits (pull)
+  int rep = 0;
+  int pushes = 0, pulls = 0;
+  int32_t last_lev = 0;  // deepest level that discovered a vertex
+  LAGR_TRY(sync_counters());
+  bool pull = false;     // direction of the previous level
+  int64_t prev_nq = 0;   // frontier size before the last level
+  for (;;) {
+    const int64_t nq = h[B_NQ], mf = h[B_MF], mu = h[B_MU];
+    const int32_t lev = (int32_t)h[B_LEV];
+    if (nq == 0) break;
+    if (lev + 1 > n) {
+      set_msg(msg, "BFS exceeded n levels");
+      return LAGR_ERR_TIMEOUT;
+    }
+    // direction of the next level (Beamer's rule: pull once a growing frontier's edges exceed the
+    // unexplored edges / alpha; push again once the frontier falls below n / beta)
+    if (push_only) pull = false;
+    else if (pull_only) pull = true;
+    else if (!pull) pull = nq > prev_nq && mf > mu / ALPHA_DO;
+    else pull = !(nq < (int64_t)n / BETA_DO);
+    prev_nq = nq;
+    if (!pull) {
+      if (rep == 1) {  // bitmap -> queue qa
+        LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p + B_NEXT, 0, sizeof(int64_t), s));
+        bfs_b2q<<<grid_for(nwords, 256), 256, 0, s>>>(fbits.p, nwords, qa.p, (unsigned long long *)(cnt.p + B_NEXT));
+        bfs_set_par<<<1, 1, 0, s>>>(cnt.p, 0);
+        LAGR_LAUNCH_CHECK();
+        LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p + B_NEXT, 0, sizeof(int64_t), s));
+        rep = 0;
+      }
+      if (nq <= SMALL_MAX) {
+        // several narrow levels in one CTA; it stops when the frontier empties, widens, or the
+        // direction rule asks for a pull (the same rule as above, so it runs at least one level)
+        bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level, parent, cnt.p,
+                                                   n, push_only ? 0 : 1);
+        LAGR_LAUNCH_CHECK();
+        LAGR_TRY(sync_counters());
+        const int32_t done = (int32_t)h[B_LEV] - lev;
+        if (h[B_EXIT] == 4) {
+          set_msg(msg, "BFS exceeded n levels");
+          return LAGR_ERR_TIMEOUT;
+        }
+        if (done <= 0) {
+          set_msg(msg, "internal: narrow-frontier kernel made no progress");
+          return LAGR_ERR_TIMEOUT;
+        }
+        pushes += done;
+        last_lev = (h[B_NQ] > 0) ? (int32_t)h[B_LEV] : (int32_t)h[B_LEV] - 1;
+      } else {
+        bfs_push<<<grid_for(nq, BFS_THREADS), BFS_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level,
+                                                                   parent, cnt.p);
+        bfs_advance<<<1, 1, 0, s>>>(cnt.p, 1);
+        LAGR_LAUNCH_CHECK();
+        LAGR_TRY(sync_counters());
+        pushes++;
+        if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
+      }
+      continue;
+    }
+    // pull level
+    if (rep == 0) {  // queue -> bitmap
+      LAGR_CUDA_TRY(cudaMemsetAsync(fbits.p, 0, nwords * sizeof(uint32_t), s));
+      bfs_q2b<<<grid_for(nq, 256), 256, 0, s>>>(qa.p, qb.p, cnt.p, fbits.p);
+      LAGR_LAUNCH_CHECK();
+      rep = 1;
+    }
+    bfs_pull<<<grid_for(nwords * 32, BFS_THREADS), BFS_THREADS, 0, s>>>(G->at_rowptr, G->at_colidx, G->rowptr, n,
+                                                                        fbits.p, nbits.p, visited.p, level, parent,
+                                                                        cnt.p);
+    bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0);
+    LAGR_LAUNCH_CHECK();
+    {
+      uint32_t *t = fbits.p;
+      fbits.p = nbits.p;
+      nbits.p = t;
+    }
+    LAGR_TRY(sync_counters());
+    pulls++;
+    if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
+  }
+  G->last_levels = last_lev + 1;
+  G->last_push_levels = pushes;
+  G->last_pull_levels = pulls;
+  if (depth) *depth = last_lev + 1;
+  clear_msg(msg);
+  return LAGR_OK;
+}
+
+extern "C" int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src, int32_t k, void *stream,
+                                char *msg) {
+  if (!level || !src) {
+    set_msg(msg, "level/src is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  LAGR_TRY(check_graph_arg(G, msg));
+  if (k < 1 || k > 64) {
+    set_msg(msg, "k must be in [1, 64], got %d", k);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  if (G->kind != LAGR_UNDIRECTED) {
+    set_msg(msg, "the 64-source BFS needs an undirected graph");
+    return LAGR_ERR_INVALID_GRAPH;
+  }
+  for (int i = 0; i < k; i++)
+    if (src[i] < 0 || src[i] >= G->n) {
+      set_msg(msg, "source %d (index %d) out of range", src[i], i);
+      return LAGR_ERR_INVALID_VALUE;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  Priv *P = nullptr;
+  LAGR_TRY(priv_get(G, s, msg, &P));
+  const int32_t n = G->n;
+  Temp<unsigned long long> seen(s), fa(s), fb(s), cnt(s);
+  Temp<int32_t> dsrc(s);
+  LAGR_TRY(seen.alloc(n, msg, "seen bitmap"));
+  LAGR_TRY(fa.alloc(n, msg, "frontier words"));
+  LAGR_TRY(fb.alloc(n, msg, "frontier words"));
+  LAGR_TRY(cnt.alloc(1, msg, "counter"));
+  LAGR_TRY(dsrc.alloc(k, msg, "sources"));
+  // the sources travel through the pinned mirror so the copy is asynchronous
+  memcpy(P->hscal, src, (size_t)k * sizeof(int32_t));
+  LAGR_CUDA_TRY(cudaMemcpyAsync(dsrc.p, P->hscal, (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  const unsigned long long kmask = (k == 64) ? ~0ull : ((1ull << k) - 1);
+  bfs64_init<<<grid_for((int64_t)k * n, 256), 256, 0, s>>>(n, k, level, seen.p, fa.p);
+  bfs64_seed<<<1, 32, 0, s>>>(n, k, dsrc.p, level, seen.p, fa.p);
+  LAGR_LAUNCH_CHECK();
+  unsigned long long *front = fa.p, *next = fb.p;
+  int32_t lev = 0;
+  for (;;) {
+    lev++;
+    if (lev > n) {
+      set_msg(msg, "BFS exceeded n levels");
+      return LAGR_ERR_TIMEOUT;
+    }
+    LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+    bfs64_pull<<<grid_for(n, BFS_THREADS), BFS_THREADS, 0, s>>>(G->rowptr, G->colidx, n, k, kmask, front, next, seen.p,
+                                                               level, lev, cnt.p);
+    LAGR_LAUNCH_CHECK();
+    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, cnt.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (P->hscal[0] == 0) break;
+    unsigned long long *t = front;
+    front = next;
+    next = t;
+  }
+  G->last_levels = lev;
+  clear_msg(msg);
+  return LAGR_OK;
+}

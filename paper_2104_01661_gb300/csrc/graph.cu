@@ -1,0 +1,379 @@
+// The graph object and its cached properties (Sec. II-A), the allocator hook and the message
+// convention (Sec. II-D), CheckGraph / Property_AT / Property_RowDegree (Sec. IV utilities).
+#include <cstdlib>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace lagr {
+
+// ---- messages ---------------------------------------------------------------------------------
+
+void set_msg(char *msg, const char *fmt, ...) {
+  if (!msg) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, LAGR_MSG_LEN, fmt, ap);
+  va_end(ap);
+}
+
+// ---- allocator hook -----------------------------------------------------------------------------
+
+static lagr_alloc_fn g_alloc = nullptr;
+static lagr_free_fn g_free = nullptr;
+static void *g_ctx = nullptr;
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+  if (g_alloc) return g_alloc(bytes, (void *)s, g_ctx);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error state of a failed allocation
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+  if (!p) return;
+  if (g_free) {
+    g_free(p, (void *)s, g_ctx);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+// ---- private state ------------------------------------------------------------------------------
+
+int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out) {
+  Priv *P = static_cast<Priv *>(G->priv);
+  if (!P) {
+    P = new Priv();
+    G->priv = P;
+  }
+  if (!P->dscal) {
+    LAGR_TRY(alloc_n(&P->dscal, LAGR_NSCAL, s, msg, "device scalars"));
+    LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal, 0, LAGR_NSCAL * sizeof(int64_t), s));
+  }
+  if (!P->hscal) {
+    LAGR_CUDA_TRY(cudaMallocHost(&P->hscal, LAGR_NHOST * sizeof(int64_t)));
+  }
+  *out = P;
+  return LAGR_OK;
+}
+
+static void free_tc_cache(Priv *P, cudaStream_t s) {
+  dev_free(P->tc_dplus, s);
+  dev_free(P->tc_listw, s);
+  dev_free(P->tc_listc, s);
+  dev_free(P->tc_heavy, s);
+  dev_free(P->tc_scan, s);
+  P->tc_heavy = nullptr;
+  P->tc_scan = nullptr;
+  P->tc_dplus = nullptr;
+  P->tc_listw = nullptr;
+  P->tc_listc = nullptr;
+  P->tc_capc = 0;
+}
+
+void priv_release(lagr_graph G, cudaStream_t s) {
+  Priv *P = static_cast<Priv *>(G->priv);
+  if (!P) return;
+  free_tc_cache(P, s);
+  dev_free(P->at_heavy, s);
+  dev_free(P->a_heavy, s);
+  dev_free(P->dscal, s);
+  if (P->hscal) {
+    cudaStreamSynchronize(s);
+    cudaFreeHost(P->hscal);
+  }
+  delete P;
+  G->priv = nullptr;
+}
+
+int check_graph_arg(lagr_graph G, char *msg) {
+  if (!G) {
+    set_msg(msg, "graph is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  if (G->n > 0 && !G->rowptr) {
+    set_msg(msg, "graph has no row pointers");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  if (G->nnz > 0 && !G->colidx) {
+    set_msg(msg, "graph has no column indices");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  return LAGR_OK;
+}
+
+// ---- CheckGraph kernels -----------------------------------------------------------------------
+
+namespace {
+
+enum CheckBits {
+  BAD_ROWPTR0 = 1,
+  BAD_MONOTONE = 2,
+  BAD_LAST = 4,
+  BAD_RANGE = 8,
+  BAD_ORDER = 16,
+  BAD_SYMMETRY = 32
+};
+
+__global__ void check_rowptr(const int32_t *__restrict__ rowptr, int32_t n, int64_t nnz, int64_t *__restrict__ flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (rowptr[i + 1] < rowptr[i]) atomicOr((unsigned long long *)&flags[0], BAD_MONOTONE);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rowptr[0] != 0) atomicOr((unsigned long long *)&flags[0], BAD_ROWPTR0);
+    if ((int64_t)rowptr[n] != nnz) atomicOr((unsigned long long *)&flags[0], BAD_LAST);
+  }
+}
+
+// one warp per row: range, strict order, self-loop count
+__global__ void check_rows(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t n,
+                           int64_t *__restrict__ flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bad = 0, diag = 0;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const int32_t b = rowptr[i], e = rowptr[i + 1];
+    for (int32_t k = b + lane; k < e; k += 32) {
+      const int32_t j = colidx[k];
+      if (j < 0 || j >= n) bad |= BAD_RANGE;
+      if (k + 1 < e && colidx[k + 1] <= j) bad |= BAD_ORDER;
+      if (j == i) diag++;
+    }
+  }
+  if (bad) atomicOr((unsigned long long *)&flags[0], bad);
+  diag = warp_sum(diag);
+  if (lane == 0 && diag) atomicAdd((unsigned long long *)&flags[1], diag);
+}
+
+__global__ void compare_arrays(const int32_t *__restrict__ a, const int32_t *__restrict__ b, int64_t len,
+                               int64_t *__restrict__ flags) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (int64_t)gridDim.x * blockDim.x)
+    if (a[k] != b[k]) {
+      atomicOr((unsigned long long *)&flags[0], BAD_SYMMETRY);
+      return;
+    }
+}
+
+__global__ void row_degree_kernel(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ deg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    deg[i] = rowptr[i + 1] - rowptr[i];
+}
+
+inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+}  // namespace
+
+}  // namespace lagr
+
+using namespace lagr;
+
+extern "C" {
+
+const char *lagr_version(void) { return "lagr-gb300 0.1 (sm_103a)"; }
+
+int lagr_set_allocator(lagr_alloc_fn alloc, lagr_free_fn free_, void *ctx) {
+  if ((alloc == nullptr) != (free_ == nullptr)) return LAGR_ERR_NULL_POINTER;
+  g_alloc = alloc;
+  g_free = free_;
+  g_ctx = ctx;
+  return LAGR_OK;
+}
+
+int lagr_graph_new(lagr_graph *G, int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                   const float *val, int32_t kind, char *msg) {
+  if (!G) {
+    set_msg(msg, "G is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  *G = nullptr;
+  if (n < 0 || nnz < 0) {
+    set_msg(msg, "negative size (n=%d, nnz=%lld)", n, (long long)nnz);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  if (nnz >= ((int64_t)1 << 31) || n == INT32_MAX) {
+    set_msg(msg, "graph too large for int32 indices (n=%d, nnz=%lld)", n, (long long)nnz);
+    return LAGR_ERR_TOO_LARGE;
+  }
+  if (kind != LAGR_UNDIRECTED && kind != LAGR_DIRECTED) {
+    set_msg(msg, "unknown graph kind %d", kind);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  if (!rowptr || (nnz > 0 && !colidx)) {
+    set_msg(msg, "rowptr/colidx is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  lagr_graph g = static_cast<lagr_graph>(calloc(1, sizeof(lagr_graph_struct)));
+  if (!g) {
+    set_msg(msg, "out of host memory");
+    return LAGR_ERR_OUT_OF_MEMORY;
+  }
+  g->n = n;
+  g->nnz = nnz;
+  g->kind = kind;
+  g->rowptr = rowptr;
+  g->colidx = colidx;
+  g->val = val;
+  g->a_pattern_is_symmetric = (kind == LAGR_UNDIRECTED) ? 1 : -1;
+  g->ndiag = -1;
+  g->u_nnz = -1;
+  g->u_order = -1;
+  g->last_levels = g->last_push_levels = g->last_pull_levels = g->last_iters = -1;
+  g->last_resid = -1.0;
+  *G = g;
+  clear_msg(msg);
+  return LAGR_OK;
+}
+
+int lagr_delete_properties(lagr_graph G, void *stream, char *msg) {
+  if (!G) {
+    set_msg(msg, "graph is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (G->at_owned) {
+    dev_free(G->at_rowptr, s);
+    dev_free(G->at_colidx, s);
+    dev_free(G->at_val, s);
+  }
+  G->at_rowptr = G->at_colidx = nullptr;
+  G->at_val = nullptr;
+  G->at_owned = 0;
+  dev_free(G->row_degree, s);
+  G->row_degree = nullptr;
+  dev_free(G->u_rowptr, s);
+  dev_free(G->u_colidx, s);
+  G->u_rowptr = G->u_colidx = nullptr;
+  G->u_nnz = -1;
+  G->u_order = -1;
+  G->ndiag = -1;
+  priv_release(G, s);
+  clear_msg(msg);
+  return LAGR_OK;
+}
+
+int lagr_graph_free(lagr_graph *G, void *stream, char *msg) {
+  if (!G || !*G) {
+    clear_msg(msg);
+    return LAGR_OK;
+  }
+  int st = lagr_delete_properties(*G, stream, msg);
+  free(*G);
+  *G = nullptr;
+  return st;
+}
+
+int lagr_property_row_degree(lagr_graph G, void *stream, char *msg) {
+  LAGR_TRY(check_graph_arg(G, msg));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!G->row_degree) {
+    int32_t *d = nullptr;
+    LAGR_TRY(alloc_n(&d, (size_t)G->n + 1, s, msg, "row degree"));
+    if (G->n > 0) row_degree_kernel<<<grid_for(G->n, 256), 256, 0, s>>>(G->rowptr, G->n, d);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      dev_free(d, s);
+      set_msg(msg, "row degree: %s", cudaGetErrorString(e));
+      return LAGR_ERR_CUDA;
+    }
+    G->row_degree = d;
+  }
+  clear_msg(msg);
+  return LAGR_OK;
+}
+
+int lagr_property_AT(lagr_graph G, void *stream, char *msg) {
+  LAGR_TRY(check_graph_arg(G, msg));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (G->at_rowptr) {
+    clear_msg(msg);
+    return LAGR_OK;
+  }
+  if (G->kind == LAGR_UNDIRECTED) {
+    G->at_rowptr = const_cast<int32_t *>(G->rowptr);
+    G->at_colidx = const_cast<int32_t *>(G->colidx);
+    G->at_val = const_cast<float *>(G->val);
+    G->at_owned = 0;
+    clear_msg(msg);
+    return LAGR_OK;
+  }
+  int32_t *rp = nullptr, *ci = nullptr;
+  float *v = nullptr;
+  int st = alloc_n(&rp, (size_t)G->n + 1, s, msg, "A' row pointers");
+  if (st == LAGR_OK) st = alloc_n(&ci, (size_t)G->nnz, s, msg, "A' column indices");
+  if (st == LAGR_OK && G->val) st = alloc_n(&v, (size_t)G->nnz, s, msg, "A' values");
+  if (st == LAGR_OK) st = transpose_csr(G->n, G->nnz, G->rowptr, G->colidx, G->val, rp, ci, v, s, msg);
+  if (st < 0) {
+    dev_free(rp, s);
+    dev_free(ci, s);
+    dev_free(v, s);
+    return st;
+  }
+  G->at_rowptr = rp;
+  G->at_colidx = ci;
+  G->at_val = v;
+  G->at_owned = 1;
+  clear_msg(msg);
+  return LAGR_OK;
+}
+
+int lagr_graph_check(lagr_graph G, void *stream, char *msg) {
+  LAGR_TRY(check_graph_arg(G, msg));
+  cudaStream_t s = (cudaStream_t)stream;
+  Priv *P = nullptr;
+  LAGR_TRY(priv_get(G, s, msg, &P));
+  const int32_t n = G->n;
+  LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal, 0, 2 * sizeof(int64_t), s));
+  check_rowptr<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, n, G->nnz, P->dscal);
+  LAGR_LAUNCH_CHECK();
+  LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  int64_t bad = P->hscal[0];
+  if (bad) {
+    set_msg(msg, "invalid row pointers:%s%s%s", (bad & BAD_ROWPTR0) ? " rowptr[0] != 0" : "",
+            (bad & BAD_MONOTONE) ? " decreasing" : "", (bad & BAD_LAST) ? " rowptr[n] != nnz" : "");
+    return LAGR_ERR_INVALID_GRAPH;
+  }
+  if (n > 0) check_rows<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(G->rowptr, G->colidx, n, P->dscal);
+  LAGR_LAUNCH_CHECK();
+  LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  bad = P->hscal[0];
+  G->ndiag = P->hscal[1];
+  if (bad) {
+    set_msg(msg, "invalid column indices:%s%s", (bad & BAD_RANGE) ? " out of range" : "",
+            (bad & BAD_ORDER) ? " row not strictly increasing (unsorted or duplicate)" : "");
+    return LAGR_ERR_INVALID_GRAPH;
+  }
+  // symmetry: A == A' entry for entry (both have sorted rows)
+  {
+    Temp<int32_t> rp(s), ci(s);
+    LAGR_TRY(rp.alloc((size_t)n + 1, msg, "check transpose"));
+    LAGR_TRY(ci.alloc((size_t)G->nnz, msg, "check transpose"));
+    LAGR_TRY(transpose_csr(n, G->nnz, G->rowptr, G->colidx, nullptr, rp.p, ci.p, nullptr, s, msg));
+    LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal, 0, sizeof(int64_t), s));
+    compare_arrays<<<grid_for(n + 1, 256), 256, 0, s>>>(G->rowptr, rp.p, (int64_t)n + 1, P->dscal);
+    if (G->nnz > 0) compare_arrays<<<grid_for(G->nnz, 256), 256, 0, s>>>(G->colidx, ci.p, G->nnz, P->dscal);
+    LAGR_LAUNCH_CHECK();
+    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  const int symmetric = P->hscal[0] == 0;
+  G->a_pattern_is_symmetric = symmetric;
+  if (G->kind == LAGR_UNDIRECTED && !symmetric) {
+    set_msg(msg, "graph is marked undirected but A != A'");
+    return LAGR_ERR_INVALID_GRAPH;
+  }
+  clear_msg(msg);
+  return LAGR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,252 @@
+// Internal helpers shared by the library's translation units: error/message
+// handling, the allocator hook, device-side warp/block primitives and the
+// private per-graph state.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "lagr.h"
+
+#define LAGR_FULL_MASK 0xffffffffu
+
+namespace lagr {
+
+// ---------------------------------------------------------------------------------------------
+// messages and error propagation (return codes: 0 ok, < 0 error, > 0 warning)
+// ---------------------------------------------------------------------------------------------
+
+void set_msg(char *msg, const char *fmt, ...);
+inline void clear_msg(char *msg) {
+  if (msg) msg[0] = 0;
+}
+
+#define LAGR_CUDA_TRY(call)                                                                   \
+  do {                                                                                        \
+    cudaError_t e__ = (call);                                                                 \
+    if (e__ != cudaSuccess) {                                                                 \
+      cudaGetLastError(); /* a failed call must not leave its code for the next check */      \
+      ::lagr::set_msg(msg, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e__)); \
+      return LAGR_ERR_CUDA;                                                                   \
+    }                                                                                         \
+  } while (0)
+
+#define LAGR_LAUNCH_CHECK() LAGR_CUDA_TRY(cudaGetLastError())
+
+#define LAGR_TRY(call)      \
+  do {                      \
+    int st__ = (call);      \
+    if (st__ < 0) return st__; \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// device memory through the user-settable allocator
+// ---------------------------------------------------------------------------------------------
+
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// allocate `count` elements of T into *p; reports LAGR_ERR_OUT_OF_MEMORY with a message
+template <class T>
+int alloc_n(T **p, size_t count, cudaStream_t s, char *msg, const char *what) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = 16;
+  *p = static_cast<T *>(dev_alloc(bytes, s));
+  if (!*p) {
+    set_msg(msg, "out of device memory allocating %s (%zu bytes)", what, bytes);
+    return LAGR_ERR_OUT_OF_MEMORY;
+  }
+  return LAGR_OK;
+}
+
+// scoped temporary: freed (stream-ordered) when it goes out of scope
+template <class T>
+struct Temp {
+  T *p = nullptr;
+  cudaStream_t s = nullptr;
+  explicit Temp(cudaStream_t st) : s(st) {}
+  ~Temp() {
+    if (p) dev_free(p, s);
+  }
+  int alloc(size_t count, char *msg, const char *what) { return alloc_n(&p, count, s, msg, what); }
+  Temp(const Temp &) = delete;
+  Temp &operator=(const Temp &) = delete;
+};
+
+// ---------------------------------------------------------------------------------------------
+// private per-graph state (behind lagr_graph_struct::priv)
+// ---------------------------------------------------------------------------------------------
+
+struct Priv {
+  // small device scratch: counters and flags used by every algorithm
+  int64_t *dscal = nullptr;  // LAGR_NSCAL int64 slots
+  int64_t *hscal = nullptr;  // pinned host mirror
+  // triangle counting: anchors of the warp class and CTA-class items (x, first neighbour)
+  int32_t *tc_dplus = nullptr;
+  int32_t *tc_listw = nullptr;
+  int2 *tc_listc = nullptr;
+  int32_t *tc_heavy = nullptr;
+  int64_t *tc_scan = nullptr;
+  int64_t tc_capc = 0;
+  // heavy rows of A' (PageRank gathers), deterministic order
+  int32_t *at_heavy = nullptr;
+  int32_t at_nheavy = -1;
+  // heavy rows of A (adjoint gathers, directed graphs)
+  int32_t *a_heavy = nullptr;
+  int32_t a_nheavy = -1;
+};
+
+enum ScalarSlot {
+  SC_ERR = 0,      // device error flag (LAGR_ERR_* or 0)
+  SC_COUNT0 = 1,   // generic counters
+  SC_COUNT1 = 2,
+  SC_COUNT2 = 3,
+  SC_COUNT3 = 4,
+  SC_COUNT4 = 5,
+  SC_COUNT5 = 6,
+  SC_COUNT6 = 7,
+  SC_COUNT7 = 8,
+  LAGR_NSCAL = 16,
+  LAGR_NHOST = 64  // int64 slots of the pinned host mirror (also stages up to 64 int32 sources)
+};
+
+int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out);
+void priv_release(lagr_graph G, cudaStream_t s);
+
+// validation shared by the entry points
+int check_graph_arg(lagr_graph G, char *msg);
+
+// ---------------------------------------------------------------------------------------------
+// triangle counting internals (tc.cu), shared with the batched path
+// ---------------------------------------------------------------------------------------------
+
+struct TcParams {
+  int chunk;  // neighbours per CTA work item
+  int wmax;   // anchors with d+ <= wmax (and moderate degree) run one per warp
+};
+TcParams tc_default_params();
+int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg);
+int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *voff, int32_t ngraphs,
+              unsigned long long *counts, bool orient, cudaStream_t s, char *msg);
+unsigned long long *tc_total_slot(Priv *P);
+
+// ---------------------------------------------------------------------------------------------
+// PageRank internals (pagerank.cu), shared with the batched path: a plan holds every buffer of
+// the unweighted (GAP form) iteration so that a fixed number of iterations can be enqueued
+// without allocation or host synchronisation.
+// ---------------------------------------------------------------------------------------------
+
+struct PrPlan;
+int pr_plan_create(PrPlan **out, lagr_graph G, Priv *P, float damping, const float *vvec, cudaStream_t s,
+                   char *msg);
+int pr_plan_enqueue(PrPlan *pl, float *out, const float *warm, int32_t iters, cudaStream_t s, char *msg);
+void pr_plan_destroy(PrPlan *pl, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------
+// scans (scan.cu)
+// ---------------------------------------------------------------------------------------------
+
+// out[0..n] = exclusive prefix sums of in[0..n-1], out[n] = total.  The total must fit int32
+// (device flag SC_ERR is not used; callers pass sizes where this holds).
+// scratch: NULL (allocated here) or scan_scratch_len(n) int64 work slots (nothing is allocated then,
+// so the call can be captured in a CUDA graph).
+int exclusive_scan(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, char *msg,
+                   int64_t *scratch = nullptr);
+int64_t scan_scratch_len(int64_t n);
+
+// stable ascending radix sort of (keys, vals) by the low `bits` bits of keys.  keys/vals are
+// sorted in place; tmp_k/tmp_v are work arrays of the same length.
+int radix_sort_pairs(int32_t *keys, int32_t *vals, int32_t *tmp_k, int32_t *tmp_v, int64_t n,
+                     int bits, cudaStream_t s, char *msg);
+
+// stable compaction of the indices i in [0, n) with deg(i) > threshold (deg from rowptr);
+// writes *list (allocated here) and its length (host value; synchronises the stream).
+int heavy_rows(const int32_t *rowptr, int32_t n, int32_t threshold, int32_t **list, int32_t *count,
+               cudaStream_t s, char *msg);
+
+// CSR -> CSC (A' by row) with rows sorted; at_val may be NULL when val is NULL.
+int transpose_csr(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                  const float *val, int32_t *at_rowptr, int32_t *at_colidx, float *at_val,
+                  cudaStream_t s, char *msg);
+
+// ---------------------------------------------------------------------------------------------
+// device primitives
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(LAGR_FULL_MASK, v, o);
+  return v;
+}
+
+// inclusive prefix sum over the 32 lanes
+__device__ __forceinline__ int warp_inclusive_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(LAGR_FULL_MASK, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// sum over a whole block; every thread must call it; result valid in every thread
+template <class T>
+__device__ T block_sum(T v, T *smem /* >= 32 elements */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  T r = (threadIdx.x < nwarps) ? smem[threadIdx.x] : T(0);
+  if (warp == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) smem[0] = r;
+  __syncthreads();
+  r = smem[0];
+  __syncthreads();
+  return r;
+}
+
+// Load-balanced walk over 32 segments (one per lane: start st, length len, a per-segment tag;
+// len 0 = empty).  Calls f(valid, tag_of_segment, position_in_segment, global_index) once per
+// round on EVERY lane, spreading the elements of all segments evenly over the 32 lanes; lanes
+// with valid == false have no element this round (their other arguments are meaningless).
+// Because every lane calls f, f may use warp-collective operations.  Warp-collective itself.
+template <class F>
+__device__ __forceinline__ void warp_segments(int st, int len, int tag, F &&f) {
+  const int lane = threadIdx.x & 31;
+  const int incl = warp_inclusive_scan(len);
+  const int total = __shfl_sync(LAGR_FULL_MASK, incl, 31);
+  for (int base = 0; base < total; base += 32) {
+    const int k = base + lane;
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int step = 0; step < 5; step++) {
+      const int mid = (lo + hi) >> 1;
+      const int v = __shfl_sync(LAGR_FULL_MASK, incl, mid);
+      if (v > k) hi = mid; else lo = mid + 1;
+    }
+    const int s = lo;
+    const int incl_s = __shfl_sync(LAGR_FULL_MASK, incl, s);
+    const int len_s = __shfl_sync(LAGR_FULL_MASK, len, s);
+    const int st_s = __shfl_sync(LAGR_FULL_MASK, st, s);
+    const int tag_s = __shfl_sync(LAGR_FULL_MASK, tag, s);
+    const int off = k - (incl_s - len_s);
+    f(k < total, tag_s, off, st_s + off);
+  }
+}
+
+}  // namespace lagr

@@ -1,0 +1,303 @@
+// Graph-store primitives: exclusive scan, stable radix sort, stable compaction of heavy rows and
+// the CSR -> CSC transpose (Property_AT, Sec. II-A).  All deterministic.
+#include "internal.cuh"
+
+namespace lagr {
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__global__ void scan_tile_sums(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ sums) {
+  __shared__ int64_t red[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  int64_t s = 0;
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+    const int64_t k = base + i;
+    if (k < n) s += in[k];
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) sums[blockIdx.x] = s;
+}
+
+// exclusive scan of the tile sums, in place, by one block of 1024 threads
+__global__ void scan_tile_offsets(int64_t *__restrict__ sums, int64_t ntiles, int32_t *__restrict__ out_total,
+                                  int64_t n) {
+  __shared__ int64_t warp_tot[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = (i < ntiles) ? sums[i] : 0;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t t = __shfl_up_sync(LAGR_FULL_MASK, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int64_t w = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(LAGR_FULL_MASK, w, o);
+        if (lane >= o) w += t;
+      }
+      warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const int64_t before = carry + (warp > 0 ? warp_tot[warp - 1] : 0);
+    if (i < ntiles) sums[i] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out_total[n] = (int32_t)carry;
+}
+
+__global__ void scan_tile_apply(const int32_t *__restrict__ in, int64_t n, const int64_t *__restrict__ offs,
+                                int32_t *__restrict__ out) {
+  __shared__ int64_t warp_tot[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int32_t v[SCAN_ITEMS];
+  int64_t tsum = 0;
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; j++) {
+    const int64_t k = base + j;
+    v[j] = (k < n) ? in[k] : 0;
+    tsum += v[j];
+  }
+  int64_t x = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(LAGR_FULL_MASK, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  int64_t before = offs[blockIdx.x];
+  for (int w = 0; w < warp; w++) before += warp_tot[w];
+  int64_t run = before + x - tsum;
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; j++) {
+    const int64_t k = base + j;
+    if (k < n) out[k] = (int32_t)run;
+    run += v[j];
+  }
+}
+
+// ---- radix sort ------------------------------------------------------------------------------
+
+constexpr int RADIX_THREADS = 256;
+constexpr int RADIX_ROUNDS = 16;
+constexpr int RADIX_TILE = RADIX_THREADS * RADIX_ROUNDS;
+constexpr int RADIX_BINS = 256;
+
+__global__ void radix_hist(const int32_t *__restrict__ keys, int64_t n, int shift, int32_t *__restrict__ hist,
+                           int nblocks) {
+  __shared__ int32_t h[RADIX_BINS];
+  for (int i = threadIdx.x; i < RADIX_BINS; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RADIX_TILE;
+  for (int i = threadIdx.x; i < RADIX_TILE; i += blockDim.x) {
+    const int64_t k = base + i;
+    if (k < n) atomicAdd(&h[((uint32_t)keys[k] >> shift) & (RADIX_BINS - 1)], 1);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RADIX_BINS; d += blockDim.x) hist[(int64_t)d * nblocks + blockIdx.x] = h[d];
+}
+
+// stable scatter: keys of this tile go, in index order within each digit, to offs[digit][block]
+__global__ void radix_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, int64_t n,
+                              int shift, const int32_t *__restrict__ offs, int nblocks,
+                              int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
+  __shared__ int32_t running[RADIX_BINS];
+  __shared__ int32_t wcnt[RADIX_THREADS / 32][RADIX_BINS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < RADIX_BINS; d += blockDim.x) running[d] = offs[(int64_t)d * nblocks + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * RADIX_TILE;
+  for (int r = 0; r < RADIX_ROUNDS; r++) {
+    for (int i = threadIdx.x; i < (RADIX_THREADS / 32) * RADIX_BINS; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t idx = base + (int64_t)r * RADIX_THREADS + threadIdx.x;
+    const bool valid = idx < n;
+    const int32_t key = valid ? keys[idx] : 0;
+    const int digit = ((uint32_t)key >> shift) & (RADIX_BINS - 1);
+    const unsigned peers = __match_any_sync(LAGR_FULL_MASK, valid ? digit : (RADIX_BINS + 1));
+    const int rank_in_warp = __popc(peers & lanemask_lt());
+    const bool leader = (__ffs(peers) - 1) == lane;
+    if (valid && leader) wcnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int32_t pos = running[digit] + rank_in_warp;
+      for (int w = 0; w < warp; w++) pos += wcnt[w][digit];
+      keys_out[pos] = key;
+      vals_out[pos] = vals[idx];
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RADIX_BINS; d += blockDim.x) {
+      int32_t add = 0;
+#pragma unroll
+      for (int w = 0; w < RADIX_THREADS / 32; w++) add += wcnt[w][d];
+      running[d] += add;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- heavy-row compaction ---------------------------------------------------------------------
+
+__global__ void mark_heavy(const int32_t *__restrict__ rowptr, int32_t n, int32_t threshold, int32_t *__restrict__ flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = (rowptr[i + 1] - rowptr[i]) > threshold;
+}
+
+__global__ void scatter_heavy(const int32_t *__restrict__ flag, const int32_t *__restrict__ pos, int32_t n,
+                              int32_t *__restrict__ list) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) list[pos[i]] = (int32_t)i;
+}
+
+// ---- transpose ------------------------------------------------------------------------------
+
+__global__ void iota_kernel(int32_t *__restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
+}
+
+// row id of every stored entry: one warp per row
+__global__ void expand_rows(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ rowid) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const int32_t b = rowptr[i], e = rowptr[i + 1];
+    for (int32_t k = b + lane; k < e; k += 32) rowid[k] = (int32_t)i;
+  }
+}
+
+__global__ void count_cols(const int32_t *__restrict__ colidx, int64_t nnz, int32_t *__restrict__ cnt) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[colidx[k]], 1);
+}
+
+__global__ void gather_transpose(const int32_t *__restrict__ perm, const int32_t *__restrict__ rowid,
+                                 const float *__restrict__ val, int64_t nnz, int32_t *__restrict__ at_colidx,
+                                 float *__restrict__ at_val) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = perm[k];
+    at_colidx[k] = rowid[e];
+    if (at_val) at_val[k] = val[e];
+  }
+}
+
+inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+}  // namespace
+
+int64_t scan_scratch_len(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+int exclusive_scan(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, char *msg, int64_t *scratch) {
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (ntiles == 0) {
+    LAGR_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int32_t), s));
+    return LAGR_OK;
+  }
+  Temp<int64_t> sums(s);
+  int64_t *sp = scratch;
+  if (!sp) {
+    LAGR_TRY(sums.alloc(ntiles, msg, "scan tile sums"));
+    sp = sums.p;
+  }
+  scan_tile_sums<<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(in, n, sp);
+  scan_tile_offsets<<<1, 1024, 0, s>>>(sp, ntiles, out, n);
+  scan_tile_apply<<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(in, n, sp, out);
+  LAGR_LAUNCH_CHECK();
+  return LAGR_OK;
+}
+
+int radix_sort_pairs(int32_t *keys, int32_t *vals, int32_t *tmp_k, int32_t *tmp_v, int64_t n, int bits,
+                     cudaStream_t s, char *msg) {
+  if (n <= 1) return LAGR_OK;
+  const int64_t nblocks = (n + RADIX_TILE - 1) / RADIX_TILE;
+  Temp<int32_t> hist(s), offs(s);
+  LAGR_TRY(hist.alloc(nblocks * RADIX_BINS, msg, "radix histogram"));
+  LAGR_TRY(offs.alloc(nblocks * RADIX_BINS + 1, msg, "radix offsets"));
+  int32_t *k_in = keys, *v_in = vals, *k_out = tmp_k, *v_out = tmp_v;
+  int passes = 0;
+  for (int shift = 0; shift < bits; shift += 8, passes++) {
+    radix_hist<<<(unsigned)nblocks, RADIX_THREADS, 0, s>>>(k_in, n, shift, hist.p, (int)nblocks);
+    LAGR_TRY(exclusive_scan(hist.p, offs.p, nblocks * RADIX_BINS, s, msg));
+    radix_scatter<<<(unsigned)nblocks, RADIX_THREADS, 0, s>>>(k_in, v_in, n, shift, offs.p, (int)nblocks, k_out,
+                                                             v_out);
+    LAGR_LAUNCH_CHECK();
+    int32_t *t = k_in; k_in = k_out; k_out = t;
+    t = v_in; v_in = v_out; v_out = t;
+  }
+  if (passes & 1) {
+    LAGR_CUDA_TRY(cudaMemcpyAsync(keys, k_in, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    LAGR_CUDA_TRY(cudaMemcpyAsync(vals, v_in, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  }
+  return LAGR_OK;
+}
+
+int heavy_rows(const int32_t *rowptr, int32_t n, int32_t threshold, int32_t **list, int32_t *count, cudaStream_t s,
+               char *msg) {
+  *list = nullptr;
+  *count = 0;
+  if (n <= 0) return LAGR_OK;
+  Temp<int32_t> flag(s), pos(s);
+  LAGR_TRY(flag.alloc(n, msg, "heavy flags"));
+  LAGR_TRY(pos.alloc((size_t)n + 1, msg, "heavy positions"));
+  mark_heavy<<<grid_for(n, 256), 256, 0, s>>>(rowptr, n, threshold, flag.p);
+  LAGR_TRY(exclusive_scan(flag.p, pos.p, n, s, msg));
+  int32_t h = 0;
+  LAGR_CUDA_TRY(cudaMemcpyAsync(&h, pos.p + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  int32_t *l = nullptr;
+  LAGR_TRY(alloc_n(&l, (size_t)h + 1, s, msg, "heavy row list"));
+  if (h > 0) scatter_heavy<<<grid_for(n, 256), 256, 0, s>>>(flag.p, pos.p, n, l);
+  LAGR_LAUNCH_CHECK();
+  *list = l;
+  *count = h;
+  return LAGR_OK;
+}
+
+int transpose_csr(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx, const float *val,
+                  int32_t *at_rowptr, int32_t *at_colidx, float *at_val, cudaStream_t s, char *msg) {
+  Temp<int32_t> cnt(s);
+  LAGR_TRY(cnt.alloc((size_t)n + 1, msg, "transpose counts"));
+  LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, ((size_t)n + 1) * sizeof(int32_t), s));
+  if (nnz > 0) count_cols<<<grid_for(nnz, 256), 256, 0, s>>>(colidx, nnz, cnt.p);
+  LAGR_LAUNCH_CHECK();
+  LAGR_TRY(exclusive_scan(cnt.p, at_rowptr, n, s, msg));
+  if (nnz == 0) return LAGR_OK;
+  Temp<int32_t> keys(s), perm(s), tk(s), tv(s), rowid(s);
+  LAGR_TRY(keys.alloc(nnz, msg, "transpose keys"));
+  LAGR_TRY(perm.alloc(nnz, msg, "transpose permutation"));
+  LAGR_TRY(tk.alloc(nnz, msg, "transpose work"));
+  LAGR_TRY(tv.alloc(nnz, msg, "transpose work"));
+  LAGR_TRY(rowid.alloc(nnz, msg, "transpose row ids"));
+  LAGR_CUDA_TRY(cudaMemcpyAsync(keys.p, colidx, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  iota_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(perm.p, nnz);
+  expand_rows<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(rowptr, n, rowid.p);
+  LAGR_LAUNCH_CHECK();
+  int bits = 1;
+  while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) bits++;
+  LAGR_TRY(radix_sort_pairs(keys.p, perm.p, tk.p, tv.p, nnz, bits, s, msg));
+  gather_transpose<<<grid_for(nnz, 256), 256, 0, s>>>(perm.p, rowid.p, val, nnz, at_colidx, at_val);
+  LAGR_LAUNCH_CHECK();
+  return LAGR_OK;
+}
+
+}  // namespace lagr

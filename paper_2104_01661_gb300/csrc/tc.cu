@@ -1,0 +1,536 @@
+// Triangle counting (Alg. 6, Sec. IV-F): t = sum(C) with C<s(L)> = L plus.pair U', fused so
+// that C is never formed (the materialised C is what the paper blames for its 3x gap to GAP).
+//
+// Orientation.  Alg. 6 relabels A by ascending degree (A(p,p)) and splits it into L = tril and
+// U = triu.  Relabelling by the stable ascending-degree permutation is the same as ordering the
+// vertices by the pair (degree, id); this file keeps the original labels and builds
+//   U(v,:) = { u in A(v,:) : key(u) > key(v) },  key = (deg, id) when sorting, id otherwise,
+// which is triu(A(p,p),1) up to the renaming.  L = U' so, for every stored (i,j) of L,
+// C(i,j) = |L(i,:) n U(j,:)| = |U(j,:) n U(i,:)|: the count of every undirected edge {x,y} is
+// the intersection of the two oriented lists.  Summed over edges this counts each triangle
+// exactly once (only its two lowest vertices' edge sees the third).
+//
+// Intersection.  Each edge {x,y} is anchored at the endpoint with the larger (d+, id); the
+// anchor's list U(x,:) goes into a shared-memory hash table once and the other endpoint's
+// (shorter) list is streamed and probed.  Anchors with short lists run one per warp; anchors
+// with long lists or many neighbours run one CTA per (anchor, chunk of neighbours).  Inside a
+// warp, the 32 lists of a batch of neighbours are walked load-balanced (warp_segments).
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace lagr {
+namespace {
+
+constexpr int ORIENT_G = 8;           // lanes per row in the orientation kernels
+constexpr int ORIENT_HEAVY = 2048;    // longer rows are oriented by a whole CTA
+constexpr int TCW_WARPS = 8;          // warps per CTA in the warp-anchor kernel
+constexpr int TCW_SLOTS = 512;        // hash slots per warp
+constexpr int TCW_MAXD = TCW_SLOTS / 2;  // warp anchors: d+ <= wmax <= 256 ...
+constexpr int TCW_MAXDEG = 4096;      // ... and degree <= 4096
+constexpr int TCC_THREADS = 512;      // CTA-anchor kernel
+constexpr int TCC_SLOTS = 8192;       // hash slots per CTA (32 KB); d+ > 4096 uses binary search
+constexpr int TCC_CHUNK = 2048;       // default neighbours per CTA work item
+constexpr int32_t EMPTY = -1;
+
+// slots of the per-graph device scalars used here
+constexpr int SL_SORT = SC_COUNT0;
+constexpr int SL_DECIDE = SC_COUNT1;
+constexpr int SL_NW = SC_COUNT2;
+constexpr int SL_NC = SC_COUNT3;
+constexpr int SL_NHEAVY = SC_COUNT4;
+constexpr int SL_QW = SC_COUNT5;
+constexpr int SL_QC = SC_COUNT6;
+constexpr int SL_TOTAL = SC_COUNT7;
+
+__device__ __forceinline__ bool keep_edge(int32_t u, int32_t v, int32_t du, int32_t dv, int sort) {
+  return sort ? (du > dv || (du == dv && u > v)) : (u > v);
+}
+
+__device__ __forceinline__ uint32_t hslot(int32_t w, int logT) {
+  return ((uint32_t)w * 0x9E3779B1u) >> (32 - logT);
+}
+
+__device__ __forceinline__ void hinsert(int32_t *tab, int logT, int32_t w) {
+  const uint32_t mask = (1u << logT) - 1;
+  uint32_t h = hslot(w, logT);
+  while (atomicCAS(&tab[h], EMPTY, w) != EMPTY) h = (h + 1) & mask;
+}
+
+__device__ __forceinline__ int hprobe(const int32_t *tab, int logT, int32_t w) {
+  const uint32_t mask = (1u << logT) - 1;
+  uint32_t h = hslot(w, logT);
+  for (;;) {
+    const int32_t v = tab[h];
+    if (v == w) return 1;
+    if (v == EMPTY) return 0;
+    h = (h + 1) & mask;
+  }
+}
+
+__device__ __forceinline__ int bsearch_has(const int32_t *__restrict__ a, int32_t len, int32_t w) {
+  int32_t lo = 0, hi = len;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (a[mid] < w) lo = mid + 1; else hi = mid;
+  }
+  return lo < len && a[lo] == w;
+}
+
+__device__ __forceinline__ int ceil_log2(int32_t x) {  // x >= 1
+  return x <= 1 ? 0 : 32 - __clz(x - 1);
+}
+
+// member graph of vertex x in a block-diagonal batch (voff has g+1 entries)
+__device__ __forceinline__ int32_t member_of(const int32_t *__restrict__ voff, int32_t g, int32_t x) {
+  int32_t lo = 0, hi = g - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (voff[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---- Alg. 6 degree heuristic: mean > 4 * median, in exact integer arithmetic -------------------
+// With X = ceil(nnz / (4n)), the lower-middle median m satisfies 4nm < nnz iff m < X iff at least
+// floor((n-1)/2) + 1 vertices have degree < X.
+__global__ void tc_decide(const int32_t *__restrict__ rowptr, int32_t n, int64_t xstar, int64_t *__restrict__ dscal) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += (int64_t)(rowptr[i + 1] - rowptr[i]) < xstar;
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long *)&dscal[SL_DECIDE], c);
+}
+
+__global__ void tc_set_mode(int32_t n, int method, int64_t *__restrict__ dscal) {
+  int sort;
+  if (method == LAGR_TC_SORT) sort = 1;
+  else if (method == LAGR_TC_NOSORT) sort = 0;
+  else sort = dscal[SL_DECIDE] >= (int64_t)((n - 1) / 2) + 1;
+  dscal[SL_SORT] = sort;
+}
+
+// ---- orientation: d+ per vertex, then the oriented rows -------------------------------------------
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (G == 32) return LAGR_FULL_MASK;
+  else return ((1u << G) - 1) << ((threadIdx.x & 31) & ~(G - 1));
+}
+
+template <int G>
+__global__ void tc_orient_count(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                const int32_t *__restrict__ deg, int32_t n, int64_t *__restrict__ dscal,
+                                int32_t *__restrict__ dplus, int32_t *__restrict__ heavy) {
+  const int sort = (int)dscal[SL_SORT];
+  const int lg = threadIdx.x & (G - 1);
+  const unsigned gm = group_mask<G>();
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
+    const int32_t b = rowptr[v], e = rowptr[v + 1];
+    if (e - b > ORIENT_HEAVY) {
+      if (lg == 0) heavy[atomicAdd((unsigned long long *)&dscal[SL_NHEAVY], 1ull)] = (int32_t)v;
+      continue;
+    }
+    const int32_t dv = e - b;
+    int cnt = 0;
+    for (int32_t k = b + lg; k < e; k += G) {
+      const int32_t u = colidx[k];
+      cnt += keep_edge(u, (int32_t)v, deg[u], dv, sort);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(gm, cnt, o);
+    if (lg == 0) dplus[v] = cnt;
+  }
+}
+
+__global__ void tc_orient_count_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                      const int32_t *__restrict__ deg, int64_t *__restrict__ dscal,
+                                      int32_t *__restrict__ dplus, const int32_t *__restrict__ heavy) {
+  __shared__ int red[32];
+  const int sort = (int)dscal[SL_SORT];
+  const int64_t nh = dscal[SL_NHEAVY];
+  for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const int32_t v = heavy[h];
+    const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
+    int cnt = 0;
+    for (int32_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+      const int32_t u = colidx[k];
+      cnt += keep_edge(u, v, deg[u], dv, sort);
+    }
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) dplus[v] = cnt;
+  }
+}
+
+template <int G>
+__global__ void tc_orient_fill(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                               const int32_t *__restrict__ deg, int32_t n, int64_t *__restrict__ dscal,
+                               const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx, int64_t ucap) {
+  const int sort = (int)dscal[SL_SORT];
+  const int lg = threadIdx.x & (G - 1);
+  const unsigned gm = group_mask<G>();
+  const unsigned lt = lanemask_lt();
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
+    const int32_t b = rowptr[v], e = rowptr[v + 1];
+    if (e - b > ORIENT_HEAVY) continue;
+    const int32_t dv = e - b;
+    int64_t out = u_rowptr[v];
+    for (int32_t base = b; base < e; base += G) {
+      const int32_t k = base + lg;
+      int32_t u = 0;
+      bool f = false;
+      if (k < e) {
+        u = colidx[k];
+        f = keep_edge(u, (int32_t)v, deg[u], dv, sort);
+      }
+      const unsigned bal = __ballot_sync(gm, f) & gm;
+      if (f) {
+        const int64_t pos = out + __popc(bal & lt);
+        if (pos < ucap) u_colidx[pos] = u;
+        else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
+      }
+      out += __popc(bal);
+    }
+  }
+}
+
+__global__ void tc_orient_fill_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                     const int32_t *__restrict__ deg, int64_t *__restrict__ dscal,
+                                     const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx,
+                                     int64_t ucap, const int32_t *__restrict__ heavy) {
+  __shared__ int wc[32];
+  const int sort = (int)dscal[SL_SORT];
+  const int64_t nh = dscal[SL_NHEAVY];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const unsigned lt = lanemask_lt();
+  for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const int32_t v = heavy[h];
+    const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
+    int64_t out = u_rowptr[v];
+    for (int32_t base = b; base < e; base += blockDim.x) {
+      const int32_t k = base + threadIdx.x;
+      int32_t u = 0;
+      bool f = false;
+      if (k < e) {
+        u = colidx[k];
+        f = keep_edge(u, v, deg[u], dv, sort);
+      }
+      const unsigned bal = __ballot_sync(LAGR_FULL_MASK, f);
+      if (lane == 0) wc[warp] = __popc(bal);
+      __syncthreads();
+      int before = 0, total = 0;
+      for (int w = 0; w < nwarps; w++) {
+        if (w < warp) before += wc[w];
+        total += wc[w];
+      }
+      if (f) {
+        const int64_t pos = out + before + __popc(bal & lt);
+        if (pos < ucap) u_colidx[pos] = u;
+        else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
+      }
+      __syncthreads();
+      out += total;
+    }
+  }
+}
+
+// ---- anchors: warp class (short list, moderate degree) and CTA items -------------------------------
+
+__global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus, int32_t n,
+                            int32_t *__restrict__ listw, int2 *__restrict__ listc, int64_t capc,
+                            int64_t *__restrict__ dscal, int wmax, int chunk) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t v = base + lane;
+    int32_t a = 0, dg = 0;
+    if (v < n) {
+      a = dplus[v];
+      dg = rowptr[v + 1] - rowptr[v];
+    }
+    const bool active = a > 0;
+    const bool is_w = active && a <= wmax && dg <= TCW_MAXDEG;
+    const int nch = (active && !is_w) ? (dg + chunk - 1) / chunk : 0;
+    // warp-class anchors
+    const unsigned bw = __ballot_sync(LAGR_FULL_MASK, is_w);
+    unsigned long long pw = 0;
+    if (lane == 0 && bw) pw = atomicAdd((unsigned long long *)&dscal[SL_NW], (unsigned long long)__popc(bw));
+    pw = __shfl_sync(LAGR_FULL_MASK, pw, 0);
+    if (is_w) listw[pw + __popc(bw & lt)] = (int32_t)v;
+    // CTA items, one per chunk of `chunk` neighbours
+    const int incl = warp_inclusive_scan(nch);
+    const int tot = __shfl_sync(LAGR_FULL_MASK, incl, 31);
+    unsigned long long pc = 0;
+    if (lane == 31 && tot) pc = atomicAdd((unsigned long long *)&dscal[SL_NC], (unsigned long long)tot);
+    pc = __shfl_sync(LAGR_FULL_MASK, pc, 31);
+    for (int c = 0; c < nch; c++) {
+      const int64_t p = (int64_t)pc + incl - nch + c;
+      if (p < capc) listc[p] = make_int2((int32_t)v, c * chunk);
+      else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
+    }
+  }
+}
+
+// ---- intersection counts --------------------------------------------------------------------------
+
+// Walk the neighbours A(x, b..e) in batches of 32; for every neighbour y anchored at x (smaller
+// (d+, id)), probe each element of U(y,:) against x's table.  Warp-collective.
+template <class Probe>
+__device__ __forceinline__ unsigned long long anchor_batches(int32_t x, int32_t a, int32_t b, int32_t e, int32_t step,
+                                                             const int32_t *__restrict__ colidx,
+                                                             const int32_t *__restrict__ u_rowptr,
+                                                             const int32_t *__restrict__ u_colidx,
+                                                             const int32_t *__restrict__ dplus, Probe &&probe) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long c = 0;
+  for (int32_t jb = b; jb < e; jb += step) {
+    const int32_t j = jb + lane;
+    int32_t st = 0, len = 0;
+    if (j < e) {
+      const int32_t y = colidx[j];
+      const int32_t dy = dplus[y];
+      if (dy > 0 && (dy < a || (dy == a && y < x))) {
+        st = u_rowptr[y];
+        len = dy;
+      }
+    }
+    warp_segments(st, len, 0, [&](bool valid, int, int, int gidx) {
+      if (valid) c += probe(u_colidx[gidx]);
+    });
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(TCW_WARPS * 32)
+    tc_count_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                  const int32_t *__restrict__ u_rowptr, const int32_t *__restrict__ u_colidx,
+                  const int32_t *__restrict__ dplus, const int32_t *__restrict__ listw, int64_t *__restrict__ dscal,
+                  const int32_t *__restrict__ voff, int32_t ngraphs, unsigned long long *__restrict__ counts) {
+  __shared__ int32_t tab_all[TCW_WARPS][TCW_SLOTS];
+  __shared__ unsigned long long red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t *tab = tab_all[warp];
+  const int64_t nw = dscal[SL_NW];
+  unsigned long long mine = 0;
+  for (;;) {
+    long long it = 0;
+    if (lane == 0) it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QW], 1ull);
+    it = __shfl_sync(LAGR_FULL_MASK, it, 0);
+    if (it >= nw) break;
+    const int32_t x = listw[it];
+    const int32_t a = dplus[x];
+    const int logT = ceil_log2(2 * a);
+    const int T = 1 << logT;
+    for (int i = lane; i < T; i += 32) tab[i] = EMPTY;
+    __syncwarp();
+    const int32_t ub = u_rowptr[x];
+    for (int i = lane; i < a; i += 32) hinsert(tab, logT, u_colidx[ub + i]);
+    __syncwarp();
+    unsigned long long c = anchor_batches(x, a, rowptr[x], rowptr[x + 1], 32, colidx, u_rowptr, u_colidx, dplus,
+                                          [&](int32_t w) { return hprobe(tab, logT, w); });
+    if (voff) {
+      c = warp_sum(c);
+      if (lane == 0 && c) atomicAdd(&counts[member_of(voff, ngraphs, x)], c);
+    } else {
+      mine += c;
+    }
+    __syncwarp();
+  }
+  if (!voff) {
+    mine = block_sum(mine, red);
+    if (threadIdx.x == 0 && mine) atomicAdd(&counts[0], mine);
+  }
+}
+
+__global__ void __launch_bounds__(TCC_THREADS)
+    tc_count_cta(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                 const int32_t *__restrict__ u_rowptr, const int32_t *__restrict__ u_colidx,
+                 const int32_t *__restrict__ dplus, const int2 *__restrict__ listc, int64_t *__restrict__ dscal,
+                 const int32_t *__restrict__ voff, int32_t ngraphs, unsigned long long *__restrict__ counts,
+                 int chunk, int64_t capc) {
+  extern __shared__ int32_t tab[];
+  __shared__ long long s_it;
+  __shared__ unsigned long long red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t nc = min(dscal[SL_NC], capc);  // never read past the list (an overflow sets SC_ERR)
+  unsigned long long mine = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QC], 1ull);
+    __syncthreads();
+    const long long it = s_it;
+    if (it >= nc) break;
+    const int2 item = listc[it];
+    const int32_t x = item.x;
+    const int32_t a = dplus[x];
+    const int32_t ub = u_rowptr[x];
+    const bool hashed = a <= TCC_SLOTS / 2;
+    const int logT = hashed ? ceil_log2(2 * a) : 0;
+    if (hashed) {
+      const int T = 1 << logT;
+      for (int i = threadIdx.x; i < T; i += blockDim.x) tab[i] = EMPTY;
+      __syncthreads();
+      for (int i = threadIdx.x; i < a; i += blockDim.x) hinsert(tab, logT, u_colidx[ub + i]);
+      __syncthreads();
+    }
+    const int32_t b = rowptr[x] + item.y;
+    const int32_t e = min(rowptr[x + 1], b + chunk);
+    unsigned long long c;
+    if (hashed)
+      c = anchor_batches(x, a, b + warp * 32, e, nwarps * 32, colidx, u_rowptr, u_colidx, dplus,
+                         [&](int32_t w) { return hprobe(tab, logT, w); });
+    else
+      c = anchor_batches(x, a, b + warp * 32, e, nwarps * 32, colidx, u_rowptr, u_colidx, dplus,
+                         [&](int32_t w) { return bsearch_has(u_colidx + ub, a, w); });
+    if (voff) {
+      c = warp_sum(c);
+      if (lane == 0 && c) atomicAdd(&counts[member_of(voff, ngraphs, x)], c);
+    } else {
+      mine += c;
+    }
+    __syncthreads();
+  }
+  if (!voff) {
+    mine = block_sum(mine, red);
+    if (threadIdx.x == 0 && mine) atomicAdd(&counts[0], mine);
+  }
+}
+
+inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+}  // namespace
+
+TcParams tc_default_params() { return TcParams{TCC_CHUNK, TCW_MAXD}; }
+
+// Allocate the orientation U (on G) and the anchor lists / orientation scratch (in the private
+// state) for the given work partition.  No kernels.
+int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
+  const int32_t n = G->n;
+  const int64_t nnz = G->nnz;
+  if (prm.wmax < 1 || prm.wmax > TCW_MAXD || prm.chunk < 32) {
+    set_msg(msg, "bad triangle-count partition (wmax=%d, chunk=%d)", prm.wmax, prm.chunk);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  const int64_t capc = 2 * (nnz / (prm.wmax + 1) + nnz / (TCW_MAXDEG + 1)) + nnz / prm.chunk + 64;
+  if (G->u_rowptr && P->tc_listw && P->tc_capc >= capc) return LAGR_OK;
+  dev_free(G->u_rowptr, s);
+  dev_free(G->u_colidx, s);
+  G->u_rowptr = G->u_colidx = nullptr;
+  dev_free(P->tc_dplus, s);
+  dev_free(P->tc_listw, s);
+  dev_free(P->tc_listc, s);
+  dev_free(P->tc_heavy, s);
+  dev_free(P->tc_scan, s);
+  P->tc_scan = nullptr;
+  P->tc_dplus = P->tc_listw = P->tc_heavy = nullptr;
+  P->tc_listc = nullptr;
+  P->tc_capc = 0;
+  G->u_order = -1;
+  LAGR_TRY(lagr_property_row_degree(G, s, msg));
+  LAGR_TRY(alloc_n(&P->tc_dplus, (size_t)n + 1, s, msg, "d+"));
+  LAGR_TRY(alloc_n(&G->u_rowptr, (size_t)n + 1, s, msg, "U row pointers"));
+  LAGR_TRY(alloc_n(&G->u_colidx, (size_t)(nnz / 2 + 1), s, msg, "U column indices"));
+  LAGR_TRY(alloc_n(&P->tc_listw, (size_t)n + 1, s, msg, "warp anchors"));
+  LAGR_TRY(alloc_n(&P->tc_listc, (size_t)capc, s, msg, "CTA anchors"));
+  LAGR_TRY(alloc_n(&P->tc_heavy, (size_t)(nnz / ORIENT_HEAVY + 1), s, msg, "heavy rows"));
+  LAGR_TRY(alloc_n(&P->tc_scan, (size_t)scan_scratch_len(n), s, msg, "scan scratch"));
+  P->tc_capc = capc;
+  return LAGR_OK;
+}
+
+// Orientation, anchor classification and the two counting kernels: kernel launches and
+// memsets only (capturable in a CUDA graph).  counts[] receives the total (or per-member totals
+// when voff != NULL; counts is zeroed here).  The Alg. 6 sort decision is taken on the device.
+int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *voff, int32_t ngraphs,
+              unsigned long long *counts, bool orient, cudaStream_t s, char *msg) {
+  const int32_t n = G->n;
+  const int64_t nnz = G->nnz;
+  const int64_t ucap = nnz / 2 + 1;
+  if (orient) {
+    LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal, 0, LAGR_NSCAL * sizeof(int64_t), s));
+    if (method == LAGR_TC_AUTO) {
+      const int64_t xstar = (nnz + 4 * (int64_t)n - 1) / (4 * (int64_t)n);
+      tc_decide<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, n, xstar, P->dscal);
+    }
+    tc_set_mode<<<1, 1, 0, s>>>(n, method, P->dscal);
+    const int ob = grid_for((int64_t)n * ORIENT_G, 256);
+    tc_orient_count<ORIENT_G><<<ob, 256, 0, s>>>(G->rowptr, G->colidx, G->row_degree, n, P->dscal, P->tc_dplus,
+                                                  P->tc_heavy);
+    tc_orient_count_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, G->row_degree, P->dscal, P->tc_dplus,
+                                                  P->tc_heavy);
+    LAGR_LAUNCH_CHECK();
+    LAGR_TRY(exclusive_scan(P->tc_dplus, G->u_rowptr, n, s, msg, P->tc_scan));
+    tc_orient_fill<ORIENT_G><<<ob, 256, 0, s>>>(G->rowptr, G->colidx, G->row_degree, n, P->dscal, G->u_rowptr,
+                                                 G->u_colidx, ucap);
+    tc_orient_fill_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, G->row_degree, P->dscal, G->u_rowptr,
+                                                 G->u_colidx, ucap, P->tc_heavy);
+    tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, P->tc_dplus, n, P->tc_listw, P->tc_listc, P->tc_capc,
+                                                 P->dscal, prm.wmax, prm.chunk);
+    LAGR_LAUNCH_CHECK();
+  } else {
+    static_assert(SL_QC == SL_QW + 1 && SL_TOTAL == SL_QC + 1, "slot layout");
+    LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal + SL_QW, 0, 3 * sizeof(int64_t), s));
+  }
+  if (counts != (unsigned long long *)(P->dscal + SL_TOTAL))
+    LAGR_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ngraphs * sizeof(unsigned long long), s));
+  const size_t smem_c = TCC_SLOTS * sizeof(int32_t);
+  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+  tc_count_cta<<<152 * 4, TCC_THREADS, smem_c, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx, P->tc_dplus,
+                                                    P->tc_listc, P->dscal, voff, ngraphs, counts, prm.chunk,
+                                                    P->tc_capc);
+  tc_count_warp<<<152 * 8, TCW_WARPS * 32, 0, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx, P->tc_dplus,
+                                                   P->tc_listw, P->dscal, voff, ngraphs, counts);
+  LAGR_LAUNCH_CHECK();
+  return LAGR_OK;
+}
+
+unsigned long long *tc_total_slot(Priv *P) { return (unsigned long long *)(P->dscal + SL_TOTAL); }
+
+}  // namespace lagr
+
+using namespace lagr;
+
+extern "C" int lagr_tc(uint64_t *ntriangles, lagr_graph G, int32_t method, void *stream, char *msg) {
+  if (!ntriangles) {
+    set_msg(msg, "ntriangles is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  LAGR_TRY(check_graph_arg(G, msg));
+  if (method != LAGR_TC_AUTO && method != LAGR_TC_SORT && method != LAGR_TC_NOSORT) {
+    set_msg(msg, "unknown triangle-count method %d", method);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  if (G->kind != LAGR_UNDIRECTED) {
+    set_msg(msg, "triangle counting needs an undirected graph");
+    return LAGR_ERR_INVALID_GRAPH;
+  }
+  *ntriangles = 0;
+  if (G->n == 0 || G->nnz == 0) {
+    clear_msg(msg);
+    return LAGR_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Priv *P = nullptr;
+  LAGR_TRY(priv_get(G, s, msg, &P));
+  const TcParams prm = tc_default_params();
+  const bool cached = G->u_rowptr && G->u_order == method && P->tc_listw;
+  LAGR_TRY(tc_alloc(G, P, prm, s, msg));
+  LAGR_TRY(tc_launch(G, P, method, prm, nullptr, 1, tc_total_slot(P), !cached, s, msg));
+  G->u_order = method;
+  LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, LAGR_NSCAL * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  if (P->hscal[SC_ERR] != 0) {
+    set_msg(msg, "oriented graph overflowed: the undirected graph is not symmetric");
+    return LAGR_ERR_INVALID_GRAPH;
+  }
+  *ntriangles = (uint64_t)P->hscal[SL_TOTAL];
+  clear_msg(msg);
+  return LAGR_OK;
+}
