@@ -233,7 +233,7 @@ def run_gpu(args):
     pr_gbs = pr_bytes_iter * iters / (pr_ms * 1e-3) / 1e9
 
     # our kernels per step, counted once with the CUDA profiler outside the timed region
-    launches = count_launches(lambda: step(rp, ci))
+    launches = None if args.no_launch_count else count_launches(lambda: step(rp, ci))
 
     out = None
     if rank == 0:
@@ -330,7 +330,7 @@ def cpu_sample(g, srcs, budget_s=20.0):
     _, k, _ = oracle.pagerank(g, DAMPING, 0.0, 2)
     secs += time.perf_counter() - t0
     edges += k * (g.nnz // 2)
-    stride = max(1, int(os.environ.get("LAGR_ORACLE_TC_STRIDE", "4096")))
+    stride = max(1, int(os.environ.get("LAGR_ORACLE_TC_STRIDE", "16")))
     _, ent, tsec = oracle.tc_sample(g, 0, stride)
     secs += tsec
     edges += ent
@@ -378,6 +378,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-launch-count", action="store_true", help="skip the profiler-based launch count")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
