@@ -206,6 +206,25 @@ int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G, int3
              int32_t flags, void *stream, char *msg);
 
 /*
+ * lagr_bfs_noalloc: the parents BFS of lagr_bfs for callers that cannot allocate device memory
+ * (the paper has no counterpart; it exists for users whose device memory is fixed up front by
+ * another owner, or who must not enter the allocator while other work runs).  It takes the
+ * undirected graph as raw device CSR arrays (no lagr_graph, whose cached properties allocate) and
+ * allocates nothing: all work space lives in one file-scope device array of the library, sized for
+ * at most LAGR_BFS_NOALLOC_MAX_N vertices (about 17 MB, held by every GPU that loads the library
+ * until the process exits).  The first call on each device looks that array's address up; make it
+ * before any stream capture.  Calls share the array: a call resets what it uses, and calls whose
+ * GPU work overlaps race, so the caller must not run two at once on one device.
+ * level, parent: device [n] outputs, either may be NULL; depth: host output or NULL; results as
+ * lagr_bfs.  Synchronises the stream.  Errors: INVALID_VALUE (n < 1, src out of range),
+ * TOO_LARGE (n > LAGR_BFS_NOALLOC_MAX_N or nnz >= 2^31), NULL_POINTER, TIMEOUT, CUDA.
+ */
+#define LAGR_BFS_NOALLOC_MAX_N (1 << 21)
+int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth, int32_t n, int64_t nnz,
+                     const int32_t *rowptr, const int32_t *colidx, int32_t src, void *stream,
+                     char *msg);
+
+/*
  * k BFS at once (1 <= k <= 64) from the sources src[0..k-1] (host array),
  * as one 64-bit bitmap frontier per vertex: the frontier matrix of Alg. 4
  * (Sec. IV-B) with ns = k and the any/or monoid in place of plus.

@@ -102,6 +102,7 @@ _SIGNATURES = {
     "lagr_tc": ([ctypes.POINTER(ctypes.c_uint64), _G, _i32, _vp, _str], ctypes.c_int),
     "lagr_bfs": ([_vp, _vp, ctypes.POINTER(_i32), _G, _i32, _i32, _vp, _str], ctypes.c_int),
     "lagr_bfs_batch64": ([_vp, _G, ctypes.POINTER(_i32), _i32, _vp, _str], ctypes.c_int),
+    "lagr_bfs_noalloc": ([_vp, _vp, ctypes.POINTER(_i32), _i32, _i64, _vp, _vp, _i32, _vp, _str], ctypes.c_int),
     "lagr_pagerank": ([_vp, ctypes.POINTER(_i32), _G, _f32, _f32, _i32, _vp, _i32, _vp, _str], ctypes.c_int),
     "lagr_pagerank_backward": ([_vp, _vp, ctypes.POINTER(_i32), _vp, _vp, _G, _f32, _f32, _i32, _vp, _i32, _vp,
                                 _str], ctypes.c_int),
@@ -261,6 +262,28 @@ def lagr_bfs(G: Graph, src: int, flags: int = 0, level=None, parent=None, want_l
                                  _stream(stream), msg)
     _check(rc, msg, "lagr_bfs")
     return level, parent, int(depth.value)
+
+
+LAGR_BFS_NOALLOC_MAX_N = 1 << 21
+
+
+def lagr_bfs_noalloc(rowptr, colidx, src: int, level, parent, stream=None):
+    """Parents BFS for callers that cannot allocate device memory: the caller passes the
+    undirected graph's device CSR and the output tensors (either may be None); the library uses
+    only its fixed built-in work array (graphs of at most LAGR_BFS_NOALLOC_MAX_N vertices) and
+    allocates nothing.  Calls must not overlap on one device.  Returns the depth."""
+    torch = _torch()
+    _dev(rowptr, torch.int32, "rowptr")
+    _dev(colidx, torch.int32, "colidx")
+    _dev(level, torch.int32, "level")
+    _dev(parent, torch.int32, "parent")
+    depth = ctypes.c_int32(0)
+    msg = _msg()
+    rc = load_library().lagr_bfs_noalloc(_ptr(level), _ptr(parent), ctypes.byref(depth), int(rowptr.numel()) - 1,
+                                         int(colidx.numel()), _ptr(rowptr), _ptr(colidx), int(src),
+                                         _stream(stream), msg)
+    _check(rc, msg, "lagr_bfs_noalloc")
+    return int(depth.value)
 
 
 def lagr_bfs_batch64(G: Graph, sources: Sequence[int], level=None, stream=None):

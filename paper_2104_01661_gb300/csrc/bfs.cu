@@ -541,3 +541,168 @@ extern "C" int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src
   clear_msg(msg);
   return LAGR_OK;
 }
+
+// ---- BFS without any device allocation -----------------------------------------------------------
+//
+// Some callers cannot allocate device memory at all: a process whose device memory is handed out
+// up front by another framework and may not grow, code that runs while the allocator must not be
+// touched (a host thread racing other work on the same context, a latency-critical loop that must
+// not block in cudaMalloc/cudaFree), or a runtime with no allocator behind it.  For them
+// lagr_bfs_noalloc keeps its whole work space (visited and frontier bitmaps, the two vertex
+// queues and the level counters) in one fixed array compiled into this file, so the caller only
+// provides the graph and the outputs.
+//
+// The array is a file-scope __device__ variable: every GPU that loads the library holds its
+// LAGR_BFS_NOALLOC_MAX_N-sized copy (about 17 MB) until the process exits.  Host code cannot use
+// the variable's name as a device address, so the first call on each device looks the address up
+// with cudaGetSymbolAddress while that device is current and remembers it; make that first call
+// before capturing a stream.  Every call on a device shares the one array and leaves its contents
+// behind; each call clears what it needs at the start, and calls whose GPU work overlaps (two
+// streams, or two host threads) race on the array and must be serialised by the caller.
+
+namespace lagr {
+namespace {
+
+constexpr int64_t NA_WORDS = LAGR_BFS_NOALLOC_MAX_N / 32;
+constexpr size_t NA_BITMAP_BYTES = (size_t)NA_WORDS * sizeof(uint32_t);
+constexpr size_t NA_QUEUE_BYTES = (size_t)LAGR_BFS_NOALLOC_MAX_N * sizeof(int32_t);
+// layout: visited | frontier bitmap | next bitmap | queue a | queue b | counters
+constexpr size_t NA_OFF_VISITED = 0;
+constexpr size_t NA_OFF_FBITS = NA_OFF_VISITED + NA_BITMAP_BYTES;
+constexpr size_t NA_OFF_NBITS = NA_OFF_FBITS + NA_BITMAP_BYTES;
+constexpr size_t NA_OFF_QA = NA_OFF_NBITS + NA_BITMAP_BYTES;
+constexpr size_t NA_OFF_QB = NA_OFF_QA + NA_QUEUE_BYTES;
+constexpr size_t NA_OFF_CNT = NA_OFF_QB + NA_QUEUE_BYTES;
+constexpr size_t NA_BYTES = NA_OFF_CNT + B_NSLOT * sizeof(int64_t);
+static_assert(NA_OFF_CNT % 8 == 0, "counter alignment");
+
+static __device__ __align__(256) unsigned char g_bfs_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 256;
+static unsigned char *g_na_ptr[NA_MAX_DEVICES];  // device address of the array, per device
+
+int noalloc_scratch(unsigned char **out, char *msg) {
+  int dev = 0;
+  LAGR_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NA_MAX_DEVICES) {
+    set_msg(msg, "device ordinal %d out of range", dev);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  if (!g_na_ptr[dev]) {
+    void *p = nullptr;
+    LAGR_CUDA_TRY(cudaGetSymbolAddress(&p, g_bfs_noalloc_scratch));
+    g_na_ptr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_na_ptr[dev];
+  return LAGR_OK;
+}
+
+}  // namespace
+}  // namespace lagr
+
+extern "C" int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth, int32_t n, int64_t nnz,
+                                const int32_t *rowptr, const int32_t *colidx, int32_t src, void *stream,
+                                char *msg) {
+  if (n < 1 || nnz < 0) {
+    set_msg(msg, "need n >= 1 and nnz >= 0 (n=%d, nnz=%lld)", n, (long long)nnz);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  if (n > LAGR_BFS_NOALLOC_MAX_N || nnz >= ((int64_t)1 << 31)) {
+    set_msg(msg, "lagr_bfs_noalloc handles at most %d vertices and < 2^31 entries (n=%d, nnz=%lld); use lagr_bfs",
+            LAGR_BFS_NOALLOC_MAX_N, n, (long long)nnz);
+    return LAGR_ERR_TOO_LARGE;
+  }
+  if (!rowptr || (nnz > 0 && !colidx)) {
+    set_msg(msg, "rowptr/colidx is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  if (src < 0 || src >= n) {
+    set_msg(msg, "source %d out of range [0, %d)", src, n);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char *base = nullptr;
+  LAGR_TRY(noalloc_scratch(&base, msg));
+  uint32_t *visited = reinterpret_cast<uint32_t *>(base + NA_OFF_VISITED);
+  uint32_t *fbits = reinterpret_cast<uint32_t *>(base + NA_OFF_FBITS);
+  uint32_t *nbits = reinterpret_cast<uint32_t *>(base + NA_OFF_NBITS);
+  int32_t *qa = reinterpret_cast<int32_t *>(base + NA_OFF_QA);
+  int32_t *qb = reinterpret_cast<int32_t *>(base + NA_OFF_QB);
+  int64_t *cnt = reinterpret_cast<int64_t *>(base + NA_OFF_CNT);
+  const int64_t nwords = ((int64_t)n + 31) / 32;
+
+  // bfs_init clears the visited words and the outputs, bfs_seed resets every counter
+  bfs_init<<<grid_for(n, 256), 256, 0, s>>>(n, level, parent, visited, nwords);
+  bfs_seed<<<1, 1, 0, s>>>(rowptr, nnz, src, level, parent, visited, qa, cnt);
+  LAGR_LAUNCH_CHECK();
+  int64_t h[B_NSLOT];
+  auto sync_counters = [&]() -> int {
+    LAGR_CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+    return LAGR_OK;
+  };
+  LAGR_TRY(sync_counters());
+  int rep = 0;  // 0: frontier in a queue, 1: in fbits
+  bool pull = false;
+  int64_t prev_nq = 0;
+  int32_t last_lev = 0;
+  for (;;) {
+    const int64_t nq = h[B_NQ], mf = h[B_MF], mu = h[B_MU];
+    const int32_t lev = (int32_t)h[B_LEV];
+    if (nq == 0) break;
+    if (lev + 1 > n) {
+      set_msg(msg, "BFS exceeded n levels");
+      return LAGR_ERR_TIMEOUT;
+    }
+    if (!pull) pull = nq > prev_nq && mf > mu / ALPHA_DO;
+    else pull = !(nq < (int64_t)n / BETA_DO);
+    prev_nq = nq;
+    if (!pull) {
+      if (rep == 1) {
+        LAGR_CUDA_TRY(cudaMemsetAsync(cnt + B_NEXT, 0, sizeof(int64_t), s));
+        bfs_b2q<<<grid_for(nwords, 256), 256, 0, s>>>(fbits, nwords, qa, (unsigned long long *)(cnt + B_NEXT));
+        bfs_set_par<<<1, 1, 0, s>>>(cnt, 0);
+        LAGR_LAUNCH_CHECK();
+        LAGR_CUDA_TRY(cudaMemsetAsync(cnt + B_NEXT, 0, sizeof(int64_t), s));
+        rep = 0;
+      }
+      if (nq <= SMALL_MAX) {
+        bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(rowptr, colidx, qa, qb, visited, level, parent, cnt, n, 1);
+        LAGR_LAUNCH_CHECK();
+        LAGR_TRY(sync_counters());
+        if (h[B_EXIT] == 4 || (int32_t)h[B_LEV] <= lev) {
+          set_msg(msg, "BFS exceeded n levels");
+          return LAGR_ERR_TIMEOUT;
+        }
+        last_lev = (h[B_NQ] > 0) ? (int32_t)h[B_LEV] : (int32_t)h[B_LEV] - 1;
+      } else {
+        bfs_push<<<grid_for(nq, BFS_THREADS), BFS_THREADS, 0, s>>>(rowptr, colidx, qa, qb, visited, level, parent,
+                                                                   cnt);
+        bfs_advance<<<1, 1, 0, s>>>(cnt, 1);
+        LAGR_LAUNCH_CHECK();
+        LAGR_TRY(sync_counters());
+        if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
+      }
+      continue;
+    }
+    if (rep == 0) {
+      LAGR_CUDA_TRY(cudaMemsetAsync(fbits, 0, nwords * sizeof(uint32_t), s));
+      bfs_q2b<<<grid_for(nq, 256), 256, 0, s>>>(qa, qb, cnt, fbits);
+      LAGR_LAUNCH_CHECK();
+      rep = 1;
+    }
+    // the graph is undirected, so A' = A: the pull scans the rows of A
+    bfs_pull<<<grid_for(nwords * 32, BFS_THREADS), BFS_THREADS, 0, s>>>(rowptr, colidx, rowptr, n, fbits, nbits,
+                                                                        visited, level, parent, cnt);
+    bfs_advance<<<1, 1, 0, s>>>(cnt, 0);
+    LAGR_LAUNCH_CHECK();
+    uint32_t *t = fbits;
+    fbits = nbits;
+    nbits = t;
+    LAGR_TRY(sync_counters());
+    if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
+  }
+  if (depth) *depth = last_lev + 1;
+  clear_msg(msg);
+  return LAGR_OK;
+}
