@@ -145,7 +145,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     L.load_library()
 
-    g = gen.rmat(SCALE, EF, seed=SEED)
+    g = gen.rmat(args.scale, EF, seed=SEED)
     srcs = [int(s) for s in gen.sources(g, NSRC, seed=SEED)]
     n, nnz = g.n, g.nnz
     m_und = nnz // 2
@@ -160,18 +160,24 @@ def run_gpu(args):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    only = args.only
+
     def step(rowptr, colidx, marks=None):
         G = L.Graph(rowptr, colidx)
+        t, iters = 0, 0
         if marks is not None:
             marks[0].record(stream)
-        t = L.lagr_tc(G, L.LAGR_TC_AUTO)
+        if only in ("all", "tc"):
+            t = L.lagr_tc(G, L.LAGR_TC_AUTO)
         if marks is not None:
             marks[1].record(stream)
-        for i, s in enumerate(srcs):
-            L.lagr_bfs(G, s, 0, level=level[i], parent=parent[i])
+        if only in ("all", "bfs"):
+            for i, s in enumerate(srcs):
+                L.lagr_bfs(G, s, 0, level=level[i], parent=parent[i])
         if marks is not None:
             marks[2].record(stream)
-        _, iters = L.lagr_pagerank(G, DAMPING, TOL, ITERMAX, rank=rank_v)
+        if only in ("all", "pr"):
+            _, iters = L.lagr_pagerank(G, DAMPING, TOL, ITERMAX, rank=rank_v)
         if marks is not None:
             marks[3].record(stream)
         G.free()
@@ -181,8 +187,8 @@ def run_gpu(args):
     t_tri, iters = step(rp, ci)
     torch.cuda.synchronize()
     deg = torch.from_numpy(np.diff(g.rowptr).astype(np.int64)).to(dev)
-    comp_edges = [int(deg[level[i] >= 0].sum().item()) // 2 for i in range(NSRC)]
-    edges_per_step = m_und + sum(comp_edges) + iters * m_und
+    comp_edges = [int(deg[level[i] >= 0].sum().item()) // 2 for i in range(NSRC)] if only in ("all", "bfs") else [0]
+    edges_per_step = (m_und if only in ("all", "tc") else 0) + sum(comp_edges) + iters * m_und
 
     for _ in range(args.warmup):
         step(rp, ci)
@@ -196,11 +202,13 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        launches0 = L.kernel_launches()
         start.record(stream)
         for k in range(args.steps):
             step(rp, ci, marks[k])
         end.record(stream)
         torch.cuda.synchronize()
+        launches_timed = L.kernel_launches() - launches0
     ms_total = max_over_ranks(start.elapsed_time(end), world)
     ms_step = ms_total / args.steps
     tc_ms = statistics.median(m[0].elapsed_time(m[1]) for m in marks)
@@ -230,10 +238,9 @@ def run_gpu(args):
     # roofline of the PageRank iteration kernel and the triangle pass, from the live timings
     hbm_peak, peak_kind = peaks()
     pr_bytes_iter = 4 * (n + 1) + 4 * nnz + 20 * n
-    pr_gbs = pr_bytes_iter * iters / (pr_ms * 1e-3) / 1e9
+    pr_gbs = pr_bytes_iter * iters / max(pr_ms * 1e-3, 1e-9) / 1e9
 
     # our kernels per step, counted once with the CUDA profiler outside the timed region
-    launches = None if args.no_launch_count else count_launches(lambda: step(rp, ci))
 
     out = None
     if rank == 0:
@@ -252,17 +259,20 @@ def run_gpu(args):
             "vs_baseline": None,
             "dtype": "int32 (TC uint64, BFS int32), f32 (PageRank)",
             "data": "synthetic (seeded R-MAT, stand-in for the paper's Kron graph)",
-            "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "sources": NSRC,
+            "config": {"workload": WORKLOAD if (only == "all" and args.scale == SCALE)
+                       else f"profiling case: rmat{args.scale}_ef{EF}, component {only} (not a bench line)",
+                       "n": n, "nnz": nnz, "sources": NSRC,
                        "l2": "inputs larger than L2 (CSR 537 MB > 129 MB); no extra flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks,
             "e2e": {"value": round(job_throughput(edges_per_step, world, e2e_ms) / 1e9, 4), "unit": "GTEPS",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches * args.steps if launches is not None else None,
+            "gpu_launches": launches_timed,
             "components": {
-                "triangles": t_tri, "tc_ms": round(tc_ms, 3), "tc_mteps": round(m_und / (tc_ms * 1e-3) / 1e6, 1),
+                "triangles": t_tri, "tc_ms": round(tc_ms, 3),
+                "tc_mteps": round(m_und / max(tc_ms * 1e-3, 1e-9) / 1e6, 1),
                 "bfs_ms_16_sources": round(bfs_ms, 3),
-                "bfs_gteps": round(sum(comp_edges) / (bfs_ms * 1e-3) / 1e9, 3),
+                "bfs_gteps": round(sum(comp_edges) / max(bfs_ms * 1e-3, 1e-9) / 1e9, 3),
                 "pagerank_ms": round(pr_ms, 3), "pagerank_iters": iters,
                 "pagerank_gbs_algorithmic": round(pr_gbs, 1),
             },
@@ -270,10 +280,145 @@ def run_gpu(args):
         out["roofline"] = roofline(args, n, nnz, iters, pr_ms, hbm_peak, peak_kind)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(g, srcs, budget_s=args.cpu_budget)
+        if not args.no_extras and only == "all":
+            del rp, ci, level, parent
+            torch.cuda.empty_cache()
+            out["extras"] = extras(L, dev, hbm_peak)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return out
+
+
+def _timed(fn, reps=3, warm=2):
+    """Median CUDA-event time of fn() in ms (fn returns after its own synchronisation or not)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def extras(L, dev, hbm_peak):
+    """The other configurations, each against its plain per-call form on the same GPU."""
+    import numpy as np
+    import torch
+
+    import gen
+    res = {}
+    pr_bytes = lambda n, nnz: 4 * (n + 1) + 4 * nnz + 20 * n  # noqa: E731
+
+    # low-skew contrast: Erdos-Renyi n = 2^23, average degree 8; 4096 x 4096 grid
+    for name, g in (("erdos_renyi_n8388608_d8", gen.erdos_renyi(1 << 23, 8, seed=SEED)),
+                    ("grid_4096x4096", gen.grid(4096, 4096))):
+        G = L.Graph.from_host(g)
+        src = int(gen.sources(g, 1, seed=SEED)[0]) if name.startswith("erdos") else 0
+        lvl = torch.empty(g.n, dtype=torch.int32, device=dev)
+        par = torch.empty(g.n, dtype=torch.int32, device=dev)
+        bfs_ms = _timed(lambda: L.lagr_bfs(G, src, 0, level=lvl, parent=par))
+        reached = int((lvl >= 0).sum())
+        comp = int(torch.from_numpy(np.diff(g.rowptr)).to(dev)[lvl >= 0].sum()) // 2
+        rank = torch.empty(g.n, dtype=torch.float32, device=dev)
+        it = [0]
+
+        def pr():
+            it[0] = L.lagr_pagerank(G, DAMPING, 0.0, 20, rank=rank)[1]
+        pr_ms = _timed(pr)
+        gbs = pr_bytes(g.n, g.nnz) * it[0] / (pr_ms * 1e-3) / 1e9
+        res[name] = {"bfs_ms": round(bfs_ms, 3), "bfs_levels": G.struct.last_levels, "bfs_reached": reached,
+                     "bfs_gteps": round(comp / (bfs_ms * 1e-3) / 1e9, 3),
+                     "pagerank_ms_per_iter": round(pr_ms / it[0], 4), "pagerank_gbs": round(gbs, 1),
+                     "pagerank_frac_hbm": round(gbs / hbm_peak, 4)}
+        G.free()
+        del G, g
+        torch.cuda.empty_cache()
+
+    # 64 sources in one bitmap frontier vs 64 plain BFS calls (R-MAT scale 20)
+    g = gen.rmat(20, 16, seed=SEED)
+    G = L.Graph.from_host(g)
+    srcs = [int(s) for s in gen.sources(g, 64, seed=SEED)]
+    lv64 = torch.empty((64, g.n), dtype=torch.int32, device=dev)
+    b_ms = _timed(lambda: L.lagr_bfs_batch64(G, srcs, level=lv64))
+    lvl = torch.empty(g.n, dtype=torch.int32, device=dev)
+
+    def plain64():
+        for s in srcs:
+            L.lagr_bfs(G, s, 0, level=lvl, want_parent=False)
+    p_ms = _timed(plain64, reps=1, warm=1)
+    res["bfs64_rmat20"] = {"batched_ms": round(b_ms, 3), "plain_64_calls_ms": round(p_ms, 3),
+                           "speedup": round(p_ms / b_ms, 2)}
+    G.free()
+    del G, g, lv64
+    torch.cuda.empty_cache()
+
+    # 512 graphs in one CUDA-graph launch vs 512 x (triangle count + 20 PageRank iterations)
+    b = gen.rmat_batch(512, seed=SEED)
+    rp = torch.from_numpy(b.rowptr).to(dev)
+    ci = torch.from_numpy(b.colidx).to(dev)
+    B = L.Batch(b.voff, rp, ci, DAMPING, 20, tile=0,
+                tune_cache=os.path.join(ROOT, "gpurun_out", "batch_tune.json") if os.path.isdir(
+                    os.path.join(ROOT, "gpurun_out")) else None)
+    ntri = torch.empty(512, dtype=torch.int64, device=dev)
+    rank = torch.empty(b.n, dtype=torch.float32, device=dev)
+    bb_ms = _timed(lambda: B.run(ntri, rank))
+    graphs = [L.Graph.from_host(p) for p in b.meta["parts"]]
+    ranks = [torch.empty(p.n, dtype=torch.float32, device=dev) for p in b.meta["parts"]]
+
+    def plain512():
+        for Gi, ri in zip(graphs, ranks):
+            L.lagr_tc(Gi)
+            L.lagr_pagerank(Gi, DAMPING, 0.0, 20, rank=ri)
+    pp_ms = _timed(plain512, reps=1, warm=1)
+    res["batch512"] = {"graphs": 512, "vertices": int(b.n), "entries": int(b.nnz), "tile": B.tile,
+                       "batched_ms": round(bb_ms, 3), "plain_512x2_calls_ms": round(pp_ms, 3),
+                       "speedup": round(pp_ms / bb_ms, 2)}
+    for Gi in graphs:
+        Gi.free()
+    B.free()
+    del graphs, ranks, B, rp, ci, b
+    torch.cuda.empty_cache()
+
+    # differentiable PageRank: forward + hand-written adjoint vs a torch autograd unroll
+    g = gen.rmat_weighted_directed(20, 16, seed=SEED)
+    rp = torch.from_numpy(g.rowptr).to(dev)
+    ci = torch.from_numpy(g.colidx).to(dev)
+    w = torch.from_numpy(g.val).to(dev).requires_grad_(True)
+    c = torch.from_numpy(gen.normal(g.n, SEED).astype(np.float32)).to(dev)
+
+    def ours():
+        w.grad = None
+        r = L.pagerank_autograd(rp, ci, w, None, DAMPING, 1e-7, 100)
+        (r * c).sum().backward()
+    torch.cuda.reset_peak_memory_stats()
+    o_ms = _timed(ours)
+    o_mem = torch.cuda.max_memory_allocated()
+    g_ours = w.grad.detach().clone()
+    rows = torch.repeat_interleave(torch.arange(g.n, device=dev), torch.from_numpy(np.diff(g.rowptr)).to(dev))
+
+    def unrolled():
+        w.grad = None
+        r = torch.full((g.n,), 1.0 / g.n, device=dev)
+        for _ in range(100):
+            # r = (1-a)/n + a W' r, written as a scatter over the CSR rows of W
+            contrib = torch.zeros(g.n, device=dev).index_add(0, ci.long(), w * r[rows])
+            r = (1 - DAMPING) / g.n + DAMPING * contrib
+        (r * c).sum().backward()
+    torch.cuda.reset_peak_memory_stats()
+    u_ms = _timed(unrolled, reps=2, warm=1)
+    u_mem = torch.cuda.max_memory_allocated()
+    rel = float((w.grad - g_ours).norm() / w.grad.norm())
+    res["adjoint_rmat20_directed"] = {"ours_fwd_bwd_ms": round(o_ms, 3), "unrolled_autograd_ms": round(u_ms, 3),
+                                      "speedup": round(u_ms / o_ms, 2), "ours_peak_mb": round(o_mem / 2**20, 1),
+                                      "unrolled_peak_mb": round(u_mem / 2**20, 1), "grad_rel_diff": round(rel, 6)}
+    return res
 
 
 def roofline(args, n, nnz, iters, pr_ms, peak, peak_kind):
@@ -281,7 +426,7 @@ def roofline(args, n, nnz, iters, pr_ms, peak, peak_kind):
     algorithmic bytes per iteration / its mean duration (CUDA events around the PageRank call,
     divided by the iterations run, so launch gaps count against it)."""
     bytes_iter = 4 * (n + 1) + 4 * nnz + 20 * n
-    ach = bytes_iter * iters / (pr_ms * 1e-3) / 1e9
+    ach = bytes_iter * iters / max(pr_ms * 1e-3, 1e-9) / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", "pr_rows_rmat22.json")
     if os.path.exists(prof):
@@ -292,21 +437,6 @@ def roofline(args, n, nnz, iters, pr_ms, peak, peak_kind):
     return {"kernel": "pr_rows (PageRank gather iteration)", "bound": "hbm", "achieved": round(ach, 1),
             "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "peak_kind": peak_kind,
             "bytes_per_launch": bytes_iter, "traffic": traffic}
-
-
-def count_launches(fn):
-    """Kernels from liblagr launched by one call of fn, by the CUDA profiler (not timed)."""
-    try:
-        import torch
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            fn()
-            torch.cuda.synchronize()
-        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
-        ours = [nm for nm in names if "lagr" in nm]
-        return len(ours) if ours else None
-    except Exception:
-        return None
 
 
 # ---------------------------------------------------------------------------------------------
@@ -380,6 +510,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-launch-count", action="store_true", help="skip the profiler-based launch count")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--only", default="all", choices=["all", "tc", "bfs", "pr"],
+                    help="run one component only (profiling captures; not a bench line)")
+    ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (profiling captures; not a bench line)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other configurations")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -298,6 +298,10 @@ int lagr_batch_free(lagr_batch *B, void *stream, char *msg);
 /* library version string */
 const char *lagr_version(void);
 
+/* Diagnostics: the number of CUDA kernels this library has launched since it was loaded (kernels
+ * replayed from a captured CUDA graph are counted once, when captured).  No paper counterpart. */
+uint64_t lagr_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,7 @@ _str = ctypes.c_char_p
 
 _SIGNATURES = {
     "lagr_version": ([], ctypes.c_char_p),
+    "lagr_kernel_launches": ([], ctypes.c_uint64),
     "lagr_set_allocator": ([_vp, _vp, _vp], ctypes.c_int),
     "lagr_graph_new": ([ctypes.POINTER(_G), _i32, _i64, _vp, _vp, _vp, _i32, _str], ctypes.c_int),
     "lagr_graph_free": ([ctypes.POINTER(_G), _vp, _str], ctypes.c_int),
@@ -430,6 +431,11 @@ def pagerank_autograd(rowptr, colidx, w, teleport=None, damping=0.85, tol=1e-7, 
                       directed=True):
     """Differentiable weighted PageRank (see PageRankFunction)."""
     return _pagerank_function().apply(rowptr, colidx, w, teleport, damping, tol, itermax, flags, directed)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(load_library().lagr_kernel_launches())
 
 
 def version() -> str:

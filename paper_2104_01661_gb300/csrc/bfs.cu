@@ -23,7 +23,8 @@ namespace {
 
 constexpr int BFS_THREADS = 256;
 constexpr int SMALL_THREADS = 1024;
-constexpr int64_t SMALL_MAX = 8192;  // frontiers up to this size stay in the single-CTA kernel
+constexpr int64_t SMALL_MAX = 8192;     // frontiers up to this many vertices ...
+constexpr int64_t SMALL_EDGES = 16384;  // ... and this many out-edges stay in the single-CTA kernel
 constexpr int ALPHA_DO = 14;
 constexpr int BETA_DO = 24;
 
@@ -111,26 +112,149 @@ __device__ __forceinline__ void push_level(const int32_t *__restrict__ rowptr, c
   }
 }
 
+// One wide push level.  The next frontier is not appended to a queue (one shared counter would
+// serialise the whole grid); a vertex claimed here gets its bit in nbits (cleared by the caller),
+// and the counts are reduced per warp once, at the end.  The frontier is read from the queue that
+// c[B_PAR] selects.
 __global__ void __launch_bounds__(BFS_THREADS)
-    bfs_push(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
-             int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
-             int32_t *__restrict__ parent, int64_t *__restrict__ c) {
+    bfs_push(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const int32_t *__restrict__ qa,
+             const int32_t *__restrict__ qb, uint32_t *__restrict__ visited, uint32_t *__restrict__ nbits,
+             int32_t *__restrict__ level, int32_t *__restrict__ parent, int64_t *__restrict__ c) {
   const int64_t nq = c[B_NQ];
   const int32_t lev = (int32_t)c[B_LEV] + 1;
-  const int par = (int)c[B_PAR];
-  const int32_t *qin = par ? qb : qa;
-  int32_t *qout = par ? qa : qb;
+  const int32_t *qin = c[B_PAR] ? qb : qa;
+  const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long mdeg = 0;
-  push_level(rowptr, colidx, qin, nq, qout, visited, level, parent, lev, warp0, nwarps,
-                    (unsigned long long *)&c[B_NEXT], mdeg);
+  unsigned long long found = 0, mdeg = 0;
+  for (int64_t wb = warp0 * 32; wb < nq; wb += nwarps * 32) {
+    const int64_t i = wb + lane;
+    int32_t u = -1, st = 0, len = 0;
+    if (i < nq) {
+      u = qin[i];
+      st = rowptr[u];
+      len = rowptr[u + 1] - st;
+    }
+    warp_segments(st, len, u, [&](bool valid, int uu, int, int gidx) {
+      if (!valid) return;
+      const int32_t v = colidx[gidx];
+      if (claim(visited, v)) {
+        atomicOr(&nbits[v >> 5], 1u << (v & 31));
+        if (level) level[v] = lev;
+        if (parent) parent[v] = uu;
+        found++;
+        mdeg += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+      }
+    });
+  }
+  found = warp_sum(found);
   mdeg = warp_sum(mdeg);
-  if ((threadIdx.x & 31) == 0 && mdeg) atomicAdd((unsigned long long *)&c[B_MNEXT], mdeg);
+  if (lane == 0) {
+    if (found) atomicAdd((unsigned long long *)&c[B_NEXT], found);
+    if (mdeg) atomicAdd((unsigned long long *)&c[B_MNEXT], mdeg);
+  }
 }
 
-// Many narrow push levels in one CTA.  Returns when the frontier is empty, grows past SMALL_MAX,
-// the direction rule asks for a pull, or max_level is reached.
+// Degrees of the frontier vertices (the input of the edge-balanced push's scan).
+__global__ void bfs_frontier_degrees(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ qa,
+                                     const int32_t *__restrict__ qb, const int64_t *__restrict__ c,
+                                     int32_t *__restrict__ fdeg) {
+  const int64_t nq = c[B_NQ];
+  const int32_t *q = c[B_PAR] ? qb : qa;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = q[i];
+    fdeg[i] = rowptr[u + 1] - rowptr[u];
+  }
+}
+
+constexpr int LB_CHUNK = 2048;  // frontier edges per CTA in the edge-balanced push
+
+// Edge-balanced wide push: CTA b expands the frontier edges [b*LB_CHUNK, (b+1)*LB_CHUNK) of the
+// concatenated adjacency lists, whatever vertices they belong to, so one hub's list is shared by
+// many CTAs instead of being walked by one warp.  offs = exclusive prefix of the frontier degrees
+// (offs[nq] = total edges).  The frontier vertices that the chunk touches are staged in shared
+// memory and each edge finds its vertex by a binary search there.  Claimed vertices get their bit
+// in nbits (cleared by the caller); counts are reduced once per warp.
+__global__ void __launch_bounds__(256)
+    bfs_push_lb(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const int32_t *__restrict__ qa,
+                const int32_t *__restrict__ qb, const int32_t *__restrict__ offs, uint32_t *__restrict__ visited,
+                uint32_t *__restrict__ nbits, int32_t *__restrict__ level, int32_t *__restrict__ parent,
+                int64_t *__restrict__ c) {
+  __shared__ int32_t s_off[LB_CHUNK + 1];
+  __shared__ int32_t s_u[LB_CHUNK + 1];
+  __shared__ int32_t s_rs[LB_CHUNK + 1];
+  __shared__ int32_t s_i0, s_cnt;
+  const int64_t nq = c[B_NQ];
+  const int32_t lev = (int32_t)c[B_LEV] + 1;
+  const int32_t *q = c[B_PAR] ? qb : qa;
+  const int32_t total = offs[nq];
+  const int32_t c0 = blockIdx.x * LB_CHUNK;
+  if (c0 >= total) return;  // uniform per CTA
+  const int32_t c1 = min(c0 + LB_CHUNK, total);
+  if (threadIdx.x == 0) {
+    // first vertex: the last i with offs[i] <= c0; last vertex: the last i with offs[i] <= c1 - 1
+    int32_t lo = 0, hi = (int32_t)nq - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (offs[mid] <= c0) lo = mid; else hi = mid - 1;
+    }
+    const int32_t i0 = lo;
+    hi = (int32_t)nq - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (offs[mid] <= c1 - 1) lo = mid; else hi = mid - 1;
+    }
+    s_i0 = i0;
+    s_cnt = lo - i0 + 1;
+  }
+  __syncthreads();
+  const int32_t i0 = s_i0, cnt = s_cnt;
+  const bool staged = cnt <= LB_CHUNK;  // vertices of degree 0 could make the range wider
+  if (staged) {
+    for (int32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int32_t u = q[i0 + t];
+      s_off[t] = offs[i0 + t];
+      s_u[t] = u;
+      s_rs[t] = rowptr[u];
+    }
+  }
+  __syncthreads();
+  unsigned long long found = 0, mdeg = 0;
+  for (int32_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+    int32_t lo = 0, hi = cnt - 1;  // last t with offs[i0 + t] <= e
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if ((staged ? s_off[mid] : offs[i0 + mid]) <= e) lo = mid; else hi = mid - 1;
+    }
+    int32_t u, rs, o;
+    if (staged) {
+      u = s_u[lo];
+      rs = s_rs[lo];
+      o = s_off[lo];
+    } else {
+      u = q[i0 + lo];
+      rs = rowptr[u];
+      o = offs[i0 + lo];
+    }
+    const int32_t v = colidx[rs + (e - o)];
+    if (claim(visited, v)) {
+      atomicOr(&nbits[v >> 5], 1u << (v & 31));
+      if (level) level[v] = lev;
+      if (parent) parent[v] = u;
+      found++;
+      mdeg += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+    }
+  }
+  found = warp_sum(found);
+  mdeg = warp_sum(mdeg);
+  if ((threadIdx.x & 31) == 0) {
+    if (found) atomicAdd((unsigned long long *)&c[B_NEXT], found);
+    if (mdeg) atomicAdd((unsigned long long *)&c[B_MNEXT], mdeg);
+  }
+}
+
+// Many narrow push levels in one CTA.  Returns when the frontier is empty, grows past SMALL_MAX
+// vertices or SMALL_EDGES out-edges, the direction rule asks for a pull, or max_level is reached.
 __global__ void __launch_bounds__(SMALL_THREADS)
     bfs_push_small(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
                    int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
@@ -144,7 +268,8 @@ __global__ void __launch_bounds__(SMALL_THREADS)
   bool first = true, growing = false;
   for (;;) {
     if (nq == 0) { exit_reason = 1; break; }
-    if (nq > SMALL_MAX) { exit_reason = 2; break; }
+    // the caller hands over only narrow frontiers; a level that widens goes back to the grid
+    if (!first && (nq > SMALL_MAX || mf > SMALL_EDGES)) { exit_reason = 2; break; }
     // the caller chose push for the first level; afterwards pull when a growing frontier's
     // edges outweigh the unexplored edges / alpha
     if (!first && allow_pull && growing && mf > mu / ALPHA_DO) { exit_reason = 3; break; }
@@ -373,13 +498,15 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
   const int32_t n = G->n;
   const int64_t nwords = ((int64_t)n + 31) / 32;
   Temp<uint32_t> visited(s), fbits(s), nbits(s);
-  Temp<int32_t> qa(s), qb(s);
+  Temp<int32_t> qa(s), qb(s), fdeg(s), offs(s);
   Temp<int64_t> cnt(s);
   LAGR_TRY(visited.alloc(nwords, msg, "visited bitmap"));
   LAGR_TRY(fbits.alloc(nwords, msg, "frontier bitmap"));
   LAGR_TRY(nbits.alloc(nwords, msg, "next frontier bitmap"));
   LAGR_TRY(qa.alloc(n, msg, "frontier queue"));
   LAGR_TRY(qb.alloc(n, msg, "frontier queue"));
+  LAGR_TRY(fdeg.alloc(n, msg, "frontier degrees"));
+  LAGR_TRY(offs.alloc((size_t)n + 1, msg, "frontier edge offsets"));
   LAGR_TRY(cnt.alloc(B_NSLOT, msg, "BFS counters"));
   bfs_init<<<grid_for(n, 256), 256, 0, s>>>(n, level, parent, visited.p, nwords);
   bfs_seed<<<1, 1, 0, s>>>(G->rowptr, G->nnz, src, level, parent, visited.p, qa.p, cnt.p);
@@ -422,7 +549,7 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
         LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p + B_NEXT, 0, sizeof(int64_t), s));
         rep = 0;
       }
-      if (nq <= SMALL_MAX) {
+      if (nq <= SMALL_MAX && mf <= SMALL_EDGES) {
         // several narrow levels in one CTA; it stops when the frontier empties, widens, or the
         // direction rule asks for a pull (the same rule as above, so it runs at least one level)
         bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level, parent, cnt.p,
@@ -441,10 +568,21 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
         pushes += done;
         last_lev = (h[B_NQ] > 0) ? (int32_t)h[B_LEV] : (int32_t)h[B_LEV] - 1;
       } else {
-        bfs_push<<<grid_for(nq, BFS_THREADS), BFS_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level,
-                                                                   parent, cnt.p);
-        bfs_advance<<<1, 1, 0, s>>>(cnt.p, 1);
+        // wide push, balanced over the frontier's edges: degrees, their prefix, one CTA per
+        // LB_CHUNK edges; the next frontier comes back as the bitmap nbits
+        bfs_frontier_degrees<<<grid_for(nq, 256), 256, 0, s>>>(G->rowptr, qa.p, qb.p, cnt.p, fdeg.p);
         LAGR_LAUNCH_CHECK();
+        LAGR_TRY(exclusive_scan(fdeg.p, offs.p, nq, s, msg));
+        LAGR_CUDA_TRY(cudaMemsetAsync(nbits.p, 0, nwords * sizeof(uint32_t), s));
+        const int64_t nchunks = (mf + LB_CHUNK - 1) / LB_CHUNK;
+        bfs_push_lb<<<(unsigned)(nchunks > 0 ? nchunks : 1), 256, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, offs.p,
+                                                                         visited.p, nbits.p, level, parent, cnt.p);
+        bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0);
+        LAGR_LAUNCH_CHECK();
+        uint32_t *t = fbits.p;
+        fbits.p = nbits.p;
+        nbits.p = t;
+        rep = 1;
         LAGR_TRY(sync_counters());
         pushes++;
         if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
@@ -666,7 +804,7 @@ extern "C" int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth,
         LAGR_CUDA_TRY(cudaMemsetAsync(cnt + B_NEXT, 0, sizeof(int64_t), s));
         rep = 0;
       }
-      if (nq <= SMALL_MAX) {
+      if (nq <= SMALL_MAX && mf <= SMALL_EDGES) {
         bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(rowptr, colidx, qa, qb, visited, level, parent, cnt, n, 1);
         LAGR_LAUNCH_CHECK();
         LAGR_TRY(sync_counters());
@@ -676,10 +814,15 @@ extern "C" int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth,
         }
         last_lev = (h[B_NQ] > 0) ? (int32_t)h[B_LEV] : (int32_t)h[B_LEV] - 1;
       } else {
-        bfs_push<<<grid_for(nq, BFS_THREADS), BFS_THREADS, 0, s>>>(rowptr, colidx, qa, qb, visited, level, parent,
-                                                                   cnt);
-        bfs_advance<<<1, 1, 0, s>>>(cnt, 1);
+        LAGR_CUDA_TRY(cudaMemsetAsync(nbits, 0, nwords * sizeof(uint32_t), s));
+        bfs_push<<<grid_for(nq, BFS_THREADS), BFS_THREADS, 0, s>>>(rowptr, colidx, qa, qb, visited, nbits, level,
+                                                                   parent, cnt);
+        bfs_advance<<<1, 1, 0, s>>>(cnt, 0);
         LAGR_LAUNCH_CHECK();
+        uint32_t *t = fbits;
+        fbits = nbits;
+        nbits = t;
+        rep = 1;
         LAGR_TRY(sync_counters());
         if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
       }

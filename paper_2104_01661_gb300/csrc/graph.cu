@@ -17,6 +17,24 @@ void set_msg(char *msg, const char *fmt, ...) {
   va_end(ap);
 }
 
+// ---- launch counter -------------------------------------------------------------------------------
+// The library is linked with --wrap=__cudaLaunchKernel, so every <<<...>>> launch in these files
+// passes through here first (the runtime entry point is declared in CUDA's crt headers).
+
+static unsigned long long g_launches = 0;
+
+}  // namespace lagr
+
+extern "C" cudaError_t __real___cudaLaunchKernel(cudaKernel_t kernel, dim3 grid, dim3 block, void **args,
+                                                 size_t smem, cudaStream_t stream);
+extern "C" cudaError_t __wrap___cudaLaunchKernel(cudaKernel_t kernel, dim3 grid, dim3 block, void **args,
+                                                 size_t smem, cudaStream_t stream) {
+  __atomic_fetch_add(&lagr::g_launches, 1ull, __ATOMIC_RELAXED);
+  return __real___cudaLaunchKernel(kernel, grid, block, args, smem, stream);
+}
+
+namespace lagr {
+
 // ---- allocator hook -----------------------------------------------------------------------------
 
 static lagr_alloc_fn g_alloc = nullptr;
@@ -65,9 +83,13 @@ static void free_tc_cache(Priv *P, cudaStream_t s) {
   dev_free(P->tc_dplus, s);
   dev_free(P->tc_listw, s);
   dev_free(P->tc_listc, s);
-  dev_free(P->tc_heavy, s);
   dev_free(P->tc_scan, s);
-  P->tc_heavy = nullptr;
+  dev_free(P->tc_rank, s);
+  dev_free(P->tc_sortbuf, s);
+  dev_free(P->tc_radix, s);
+  dev_free(P->tc_radix_scan, s);
+  P->tc_rank = P->tc_sortbuf = P->tc_radix = nullptr;
+  P->tc_radix_scan = nullptr;
   P->tc_scan = nullptr;
   P->tc_dplus = nullptr;
   P->tc_listw = nullptr;
@@ -79,8 +101,12 @@ void priv_release(lagr_graph G, cudaStream_t s) {
   Priv *P = static_cast<Priv *>(G->priv);
   if (!P) return;
   free_tc_cache(P, s);
-  dev_free(P->at_heavy, s);
-  dev_free(P->a_heavy, s);
+  for (RowPlan *rp : {&P->pr_at, &P->pr_a}) {
+    dev_free(rp->blk, s);
+    dev_free(rp->heavy, s);
+    dev_free(rp->hc_off, s);
+    dev_free(rp->hc_row, s);
+  }
   dev_free(P->dscal, s);
   if (P->hscal) {
     cudaStreamSynchronize(s);
@@ -179,6 +205,8 @@ using namespace lagr;
 extern "C" {
 
 const char *lagr_version(void) { return "lagr-gb300 0.1 (sm_103a)"; }
+
+uint64_t lagr_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 int lagr_set_allocator(lagr_alloc_fn alloc, lagr_free_fn free_, void *ctx) {
   if ((alloc == nullptr) != (free_ == nullptr)) return LAGR_ERR_NULL_POINTER;

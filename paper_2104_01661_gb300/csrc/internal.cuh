@@ -80,6 +80,26 @@ struct Temp {
 // private per-graph state (behind lagr_graph_struct::priv)
 // ---------------------------------------------------------------------------------------------
 
+// Partition of the rows of a CSR for the row-block kernels (PageRank gathers, the triangle-count
+// orientation): rows of at most ROW_HEAVY entries are grouped into blocks of at most ROW_UNITS
+// units (a unit is one entry or one row), one CTA each; longer rows are listed in `heavy`
+// (ascending) and handled by a CTA each.  A block's entries are contiguous, at most
+// ROW_UNITS + ROW_HEAVY of them unless the block holds a heavy row.
+constexpr int ROW_UNITS = 4096;
+constexpr int ROW_HEAVY = 4096;
+struct RowPlan {
+  int32_t *blk = nullptr;    // [nblk + 1] first row of each block, blk[nblk] = n
+  int32_t nblk = -1;         // -1 until built
+  int32_t *heavy = nullptr;  // [nheavy] rows longer than the threshold
+  int32_t nheavy = 0;
+  // heavy rows are cut into chunks of ROW_HCHUNK entries: chunks hc_off[h] .. hc_off[h+1]-1
+  // belong to heavy[h]; hc_row[c] is the heavy index of chunk c
+  int32_t *hc_off = nullptr;  // [nheavy + 1]
+  int32_t *hc_row = nullptr;  // [nhc]
+  int32_t nhc = 0;
+};
+constexpr int ROW_HCHUNK = 8192;
+
 struct Priv {
   // small device scratch: counters and flags used by every algorithm
   int64_t *dscal = nullptr;  // LAGR_NSCAL int64 slots
@@ -88,15 +108,14 @@ struct Priv {
   int32_t *tc_dplus = nullptr;
   int32_t *tc_listw = nullptr;
   int2 *tc_listc = nullptr;
-  int32_t *tc_heavy = nullptr;
+  int32_t *tc_rank = nullptr;   // degree rank (the A(p,p) labels of Alg. 6) or the id
+  int32_t *tc_sortbuf = nullptr;  // 4n keys/values/work for the rank sort
+  int32_t *tc_radix = nullptr;  // radix scratch
+  int64_t *tc_radix_scan = nullptr;
   int64_t *tc_scan = nullptr;
   int64_t tc_capc = 0;
-  // heavy rows of A' (PageRank gathers), deterministic order
-  int32_t *at_heavy = nullptr;
-  int32_t at_nheavy = -1;
-  // heavy rows of A (adjoint gathers, directed graphs)
-  int32_t *a_heavy = nullptr;
-  int32_t a_nheavy = -1;
+  // row plans of the PageRank gathers over the rows of A' (forward) and of A (adjoint)
+  RowPlan pr_at, pr_a;
 };
 
 enum ScalarSlot {
@@ -114,6 +133,9 @@ enum ScalarSlot {
 };
 
 int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out);
+
+// build (once; no-op when pl->nblk >= 0) the row plan of a CSR.  Synchronises the stream.
+int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg);
 void priv_release(lagr_graph G, cudaStream_t s);
 
 // validation shared by the entry points
@@ -158,9 +180,13 @@ int exclusive_scan(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, c
 int64_t scan_scratch_len(int64_t n);
 
 // stable ascending radix sort of (keys, vals) by the low `bits` bits of keys.  keys/vals are
-// sorted in place; tmp_k/tmp_v are work arrays of the same length.
+// sorted in place; tmp_k/tmp_v are work arrays of the same length.  scratch: NULL or
+// radix_scratch_len(n) int32 slots, scan_scratch: NULL or scan_scratch_len(radix_scratch_len(n))
+// int64 slots (with both given nothing is allocated).
+int64_t radix_scratch_len(int64_t n);
 int radix_sort_pairs(int32_t *keys, int32_t *vals, int32_t *tmp_k, int32_t *tmp_v, int64_t n,
-                     int bits, cudaStream_t s, char *msg);
+                     int bits, cudaStream_t s, char *msg, int32_t *scratch = nullptr,
+                     int64_t *scan_scratch = nullptr);
 
 // stable compaction of the indices i in [0, n) with deg(i) > threshold (deg from rowptr);
 // writes *list (allocated here) and its length (host value; synchronises the stream).

@@ -1,17 +1,24 @@
 // PageRank (Alg. 3, Sec. IV-C) and its adjoint.
 //
-// One launch per iteration gathers a whole row of A' (a "pull" SpMV over the CSC) per group of
-// G lanes and fuses every other step of Alg. 3 into it: the teleport assignment, the
-// accumulation r += A' plus.second w, the next w = damping * r / d_out (eWiseMult), and the
-// per-block partial sums of |t - r| (the apply(abs) + reduce of the stopping test) and of the
-// dangling mass.  Rows longer than PR_HEAVY are gathered by one CTA each.  A one-block kernel
-// folds the partials in a fixed order (so results do not depend on scheduling), decides
-// convergence on the device and prepares the next iteration's scalar; later launches in the
-// same batch see the flag and return at once.
+// One iteration is one gather over the rows of A' (a "pull" SpMV over the CSC) that fuses every
+// other step of Alg. 3: the teleport assignment, the accumulation r += A' plus.second w, the next
+// w = damping * r / d_out (eWiseMult), and per-CTA partial sums of |t - r| (the apply(abs) +
+// reduce of the stopping test) and of the dangling mass.
 //
-// MODE 0: unweighted forward    r_i   = v_i c + sum_{j in A'(i,:)} w_j,  w_j = damping t_j / d_out(j)
-// MODE 1: weighted forward      r_i   = v_i c + damping sum_j W(j,i) t_j
-// MODE 2: adjoint (rows of W)   l'_i  = g_i + damping sum_j W(i,j) l_j [+ damping (v.l) if i dangling]
+// Work partition (a RowPlan, built once per graph and cached): rows of at most PR_HEAVY entries
+// are grouped into blocks of at most PR_UNITS units, a unit being one entry or one row (so long
+// runs of isolated vertices cannot pile up in one block).  A block's entries are contiguous in
+// the CSR, so its CTA loads colidx fully coalesced and keeps many independent gathers x[colidx]
+// in flight, staging the gathered values in shared memory; each short row is then summed by one
+// thread and each longer row by one warp, in a fixed order (deterministic results).  Rows longer
+// than PR_HEAVY are cut into fixed chunks, summed by trailing CTAs of the same launch, and a small
+// kernel adds each such row's chunk sums in chunk order.  A one-block kernel folds the per-CTA partials in a
+// fixed order, decides convergence on the device and prepares the next iteration's scalar; later
+// launches of the same batch see the flag and return at once.
+//
+// MODE 0: unweighted forward    r_i  = v_i c + sum_{j in A'(i,:)} w_j,   w_j = damping t_j / d_out(j)
+// MODE 1: weighted forward      r_i  = v_i c + damping sum_j W(j,i) t_j
+// MODE 2: adjoint (rows of W)   l'_i = g_i + damping sum_j W(i,j) l_j [+ damping (v.l) if i dangling]
 // where c = (1 - damping) [+ damping * (dangling mass of t) with LAGR_PR_DANGLING].
 #include <cmath>
 #include <cstring>
@@ -22,10 +29,12 @@ namespace lagr {
 namespace {
 
 constexpr int PR_THREADS = 256;
-constexpr int PR_BLOCKS = 152 * 8;   // fixed grid: the partial-sum layout does not depend on n
-constexpr int PR_HEAVY = 4096;       // rows longer than this are gathered by a CTA
-constexpr int PR_HEAVY_BLOCKS = 152;
-constexpr int PR_CHUNK = 8;          // iterations launched between host checks
+constexpr int PR_UNITS = ROW_UNITS;                 // units (entries + rows) per row block
+constexpr int PR_HEAVY = ROW_HEAVY;                 // longer rows: one CTA each
+constexpr int PR_STAGE = PR_UNITS + PR_HEAVY + 64;  // staged values per block (bound + slack)
+constexpr int PR_SHORT = 32;                        // rows up to this length: one thread each
+constexpr int PR_CHUNK = 8;                         // iterations launched between host checks
+constexpr int PR_INIT_BLOCKS = 152 * 8;
 
 struct PrState {
   double resid;   // last L1 change
@@ -36,12 +45,6 @@ struct PrState {
   int pad;
 };
 
-template <int G>
-__device__ __forceinline__ unsigned group_mask() {
-  if constexpr (G == 32) return LAGR_FULL_MASK;
-  else return ((1u << G) - 1) << ((threadIdx.x & 31) & ~(G - 1));
-}
-
 // per-vertex damping / out-degree (0 for dangling rows) from the rows of A
 __global__ void pr_scale(const int32_t *__restrict__ rowptr, int32_t n, float damping, float *__restrict__ sc) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -49,6 +52,8 @@ __global__ void pr_scale(const int32_t *__restrict__ rowptr, int32_t n, float da
     sc[i] = d > 0 ? damping / (float)d : 0.0f;
   }
 }
+
+// ---- the iteration --------------------------------------------------------------------------------
 
 // r0 (uniform 1/n unless warm), w0 = r0 * sc, partial sums of the dangling mass of r0 (aux)
 // MODE 2: l0 = g, aux = v . g
@@ -69,86 +74,170 @@ __global__ void pr_init(int32_t n, float *__restrict__ x, float *__restrict__ w,
   if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(0.0, aux);
 }
 
+struct IterArgs {
+  const int32_t *rowptr, *colidx;
+  const float *val;   // MODE 1/2
+  const float *x;     // gathered vector (w for MODE 0, t for MODE 1, lambda for MODE 2)
+  const float *prev;  // previous iterate (residual)
+  float *out;         // new iterate
+  float *wout;        // MODE 0: new w
+  const float *sc;    // damping / d_out, 0 on dangling rows
+  const float *vvec;  // teleport vector or NULL (uniform vuni)
+  float vuni;
+  const float *gvec;  // MODE 2: dL/dr
+  float damping;
+  int dangling;
+  float *hpart;       // partial sums of the heavy-row chunks
+};
+
 template <int MODE>
-__device__ __forceinline__ void pr_row_out(int64_t i, float acc, float damping, float coef, int dangling,
-                                           const float *__restrict__ prev, float *__restrict__ out,
-                                           float *__restrict__ wout, const float *__restrict__ sc,
-                                           const float *__restrict__ vvec, float vuni, const float *__restrict__ gvec,
-                                           double &resid, double &aux) {
-  const float vi = vvec ? vvec[i] : vuni;
-  const float s = sc[i];
+__device__ __forceinline__ float gather_one(const IterArgs &a, int32_t k) {
+  const int32_t j = __ldg(&a.colidx[k]);
+  if (MODE == 0) return __ldg(&a.x[j]);
+  return __ldg(&a.val[k]) * __ldg(&a.x[j]);
+}
+
+template <int MODE>
+__device__ __forceinline__ void row_out(const IterArgs &a, int32_t i, float acc, float coef, double &resid,
+                                        double &aux) {
+  const float vi = a.vvec ? a.vvec[i] : a.vuni;
+  const float s = a.sc[i];
   float r;
   if (MODE == 0) {
     r = vi * coef + acc;
-    wout[i] = r * s;
+    a.wout[i] = r * s;
   } else if (MODE == 1) {
-    r = vi * coef + damping * acc;
+    r = vi * coef + a.damping * acc;
   } else {
-    r = gvec[i] + damping * acc;
-    if (dangling && s == 0.0f) r += coef;
+    r = a.gvec[i] + a.damping * acc;
+    if (a.dangling && s == 0.0f) r += coef;
   }
-  out[i] = r;
-  resid += fabs((double)prev[i] - (double)r);
+  a.out[i] = r;
+  resid += fabs((double)a.prev[i] - (double)r);
   if (MODE == 2) aux += (double)vi * (double)r;
   else if (s == 0.0f) aux += (double)r;
 }
 
-template <int G, int MODE>
+// one CTA per row block
+template <int MODE>
 __global__ void __launch_bounds__(PR_THREADS)
-    pr_rows(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-            const float *__restrict__ val, const float *__restrict__ x, const float *__restrict__ prev,
-            float *__restrict__ out, float *__restrict__ wout, const float *__restrict__ sc,
-            const float *__restrict__ vvec, float vuni, const float *__restrict__ gvec, float damping, int dangling,
-            const PrState *__restrict__ st, double2 *__restrict__ partials) {
+    pr_stream(IterArgs a, const int32_t *__restrict__ blk, int32_t nblk, const int32_t *__restrict__ heavy,
+              const int32_t *__restrict__ hc_off, const int32_t *__restrict__ hc_row, const PrState *__restrict__ st,
+              double2 *__restrict__ partials) {
+  __shared__ float stage[PR_STAGE];
+  // a row longer than PR_SHORT spends more than PR_SHORT + 1 of the block's PR_UNITS units
+  __shared__ int32_t longrows[PR_UNITS / (PR_SHORT + 1) + 2];
+  __shared__ int n_long;
   __shared__ double red[32];
   if (st->done) return;  // uniform over the grid
   const float coef = st->coef;
-  const int lg = threadIdx.x & (G - 1);
-  const unsigned gm = group_mask<G>();
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
-  double resid = 0.0, aux = 0.0;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < n; i += groups) {
-    const int32_t b = rowptr[i], e = rowptr[i + 1];
-    if (e - b > PR_HEAVY) continue;
+  if ((int32_t)blockIdx.x >= nblk) {
+    // the trailing CTAs each sum one chunk of ROW_HCHUNK entries of a row longer than PR_HEAVY,
+    // while the row blocks are still being processed; pr_heavy_finish adds the chunks up
+    const int32_t cidx = blockIdx.x - nblk;
+    const int32_t h = hc_row[cidx];
+    const int32_t i = heavy[h];
+    const int32_t b = a.rowptr[i] + (cidx - hc_off[h]) * ROW_HCHUNK;
+    const int32_t e = min(a.rowptr[i + 1], b + ROW_HCHUNK);
     float acc = 0.0f;
-    for (int32_t k = b + lg; k < e; k += G) {
-      const int32_t j = colidx[k];
-      acc += (MODE == 0) ? __ldg(&x[j]) : __ldg(&val[k]) * __ldg(&x[j]);
+    int32_t k = b + threadIdx.x;
+    for (; k + 3 * PR_THREADS < e; k += 4 * PR_THREADS) {
+      const float g0 = gather_one<MODE>(a, k), g1 = gather_one<MODE>(a, k + PR_THREADS);
+      const float g2 = gather_one<MODE>(a, k + 2 * PR_THREADS), g3 = gather_one<MODE>(a, k + 3 * PR_THREADS);
+      acc += (g0 + g1) + (g2 + g3);
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gm, acc, o);
-    if (lg == 0)
-      pr_row_out<MODE>(i, acc, damping, coef, dangling, prev, out, wout, sc, vvec, vuni, gvec, resid, aux);
+    for (; k < e; k += PR_THREADS) acc += gather_one<MODE>(a, k);
+    acc = block_sum(acc, reinterpret_cast<float *>(stage));
+    if (threadIdx.x == 0) a.hpart[cidx] = acc;
+    return;
+  }
+  const int32_t r0 = blk[blockIdx.x], r1 = blk[blockIdx.x + 1];
+  double resid = 0.0, aux = 0.0;
+  if (threadIdx.x == 0) n_long = 0;
+  const int32_t e0 = a.rowptr[r0], e1 = a.rowptr[r1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (e1 - e0 <= PR_STAGE) {
+    // stage the gathered values of the whole block: colidx coalesced, 4 gathers per thread in flight
+    int32_t k = e0 + threadIdx.x;
+    for (; k + 3 * PR_THREADS < e1; k += 4 * PR_THREADS) {
+      const float g0 = gather_one<MODE>(a, k);
+      const float g1 = gather_one<MODE>(a, k + PR_THREADS);
+      const float g2 = gather_one<MODE>(a, k + 2 * PR_THREADS);
+      const float g3 = gather_one<MODE>(a, k + 3 * PR_THREADS);
+      stage[k - e0] = g0;
+      stage[k + PR_THREADS - e0] = g1;
+      stage[k + 2 * PR_THREADS - e0] = g2;
+      stage[k + 3 * PR_THREADS - e0] = g3;
+    }
+    for (; k < e1; k += PR_THREADS) stage[k - e0] = gather_one<MODE>(a, k);
+    __syncthreads();
+    // short rows: one thread each; longer rows: queued for the warps
+    for (int32_t i = r0 + threadIdx.x; i < r1; i += PR_THREADS) {
+      const int32_t b = a.rowptr[i], e = a.rowptr[i + 1];
+      if (e - b <= PR_SHORT) {
+        float acc = 0.0f;
+        for (int32_t q = b; q < e; q++) acc += stage[q - e0];
+        row_out<MODE>(a, i, acc, coef, resid, aux);
+      } else if (e - b <= PR_HEAVY) {
+        longrows[atomicAdd(&n_long, 1)] = i;
+      }
+    }
+    __syncthreads();
+    for (int q = warp; q < n_long; q += PR_THREADS / 32) {
+      const int32_t i = longrows[q];
+      const int32_t b = a.rowptr[i], e = a.rowptr[i + 1];
+      float acc = 0.0f;
+      for (int32_t k2 = b + lane; k2 < e; k2 += 32) acc += stage[k2 - e0];
+      acc = warp_sum(acc);
+      if (lane == 0) row_out<MODE>(a, i, acc, coef, resid, aux);
+    }
+  } else {
+    // the block holds a row longer than PR_HEAVY (gathered elsewhere), so its entries are not one
+    // short run: short rows one thread each straight from memory, longer rows one warp each
+    __syncthreads();  // n_long is initialised
+    for (int32_t i = r0 + threadIdx.x; i < r1; i += PR_THREADS) {
+      const int32_t b = a.rowptr[i], e = a.rowptr[i + 1];
+      if (e - b <= PR_SHORT) {
+        float acc = 0.0f;
+        for (int32_t q = b; q < e; q++) acc += gather_one<MODE>(a, q);
+        row_out<MODE>(a, i, acc, coef, resid, aux);
+      } else if (e - b <= PR_HEAVY) {
+        longrows[atomicAdd(&n_long, 1)] = i;
+      }
+    }
+    __syncthreads();
+    for (int q = warp; q < n_long; q += PR_THREADS / 32) {
+      const int32_t i = longrows[q];
+      const int32_t b = a.rowptr[i], e = a.rowptr[i + 1];
+      float acc = 0.0f;
+      for (int32_t k2 = b + lane; k2 < e; k2 += 32) acc += gather_one<MODE>(a, k2);
+      acc = warp_sum(acc);
+      if (lane == 0) row_out<MODE>(a, i, acc, coef, resid, aux);
+    }
   }
   resid = block_sum(resid, red);
   aux = block_sum(aux, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(resid, aux);
 }
 
+// the rows longer than PR_HEAVY: add each row's chunk sums in chunk order, then the row's output
+constexpr int PR_HF_THREADS = 256;
 template <int MODE>
-__global__ void __launch_bounds__(512)
-    pr_rows_heavy(const int32_t *__restrict__ heavy, int32_t nheavy, const int32_t *__restrict__ rowptr,
-                  const int32_t *__restrict__ colidx, const float *__restrict__ val, const float *__restrict__ x,
-                  const float *__restrict__ prev, float *__restrict__ out, float *__restrict__ wout,
-                  const float *__restrict__ sc, const float *__restrict__ vvec, float vuni,
-                  const float *__restrict__ gvec, float damping, int dangling, const PrState *__restrict__ st,
-                  double2 *__restrict__ partials) {
-  __shared__ float redf[32];
+__global__ void __launch_bounds__(PR_HF_THREADS)
+    pr_heavy_finish(IterArgs a, const int32_t *__restrict__ heavy, int32_t nheavy, const int32_t *__restrict__ hc_off,
+                    const PrState *__restrict__ st, double2 *__restrict__ partials) {
+  __shared__ double red[32];
   if (st->done) return;
   const float coef = st->coef;
   double resid = 0.0, aux = 0.0;
-  for (int32_t h = blockIdx.x; h < nheavy; h += gridDim.x) {
-    const int32_t i = heavy[h];
-    const int32_t b = rowptr[i], e = rowptr[i + 1];
+  const int32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h < nheavy) {
     float acc = 0.0f;
-    for (int32_t k = b + threadIdx.x; k < e; k += blockDim.x) {
-      const int32_t j = colidx[k];
-      acc += (MODE == 0) ? __ldg(&x[j]) : __ldg(&val[k]) * __ldg(&x[j]);
-    }
-    acc = block_sum(acc, redf);
-    if (threadIdx.x == 0)
-      pr_row_out<MODE>(i, acc, damping, coef, dangling, prev, out, wout, sc, vvec, vuni, gvec, resid, aux);
+    for (int32_t c = hc_off[h]; c < hc_off[h + 1]; c++) acc += a.hpart[c];
+    row_out<MODE>(a, heavy[h], acc, coef, resid, aux);
   }
+  resid = block_sum(resid, red);
+  aux = block_sum(aux, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(resid, aux);
 }
 
@@ -178,28 +267,26 @@ __global__ void pr_finalize(const double2 *__restrict__ partials, int np, PrStat
   }
 }
 
-// dL/dW(i,j) = damping r_i lambda_j over the rows of W (G lanes per row; heavy rows by a CTA)
-template <int G>
-__global__ void pr_edge_grad(int32_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                             const float *__restrict__ r, const float *__restrict__ lam, float damping,
-                             float *__restrict__ dw) {
-  const int lg = threadIdx.x & (G - 1);
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < n; i += groups) {
-    const int32_t b = rowptr[i], e = rowptr[i + 1];
-    if (e - b > PR_HEAVY) continue;
-    const float ri = damping * r[i];
-    for (int32_t k = b + lg; k < e; k += G) dw[k] = ri * __ldg(&lam[colidx[k]]);
-  }
-}
-
-__global__ void pr_edge_grad_heavy(const int32_t *__restrict__ heavy, int32_t nheavy, const int32_t *__restrict__ rowptr,
-                                   const int32_t *__restrict__ colidx, const float *__restrict__ r,
-                                   const float *__restrict__ lam, float damping, float *__restrict__ dw) {
-  for (int32_t h = blockIdx.x; h < nheavy; h += gridDim.x) {
-    const int32_t i = heavy[h];
-    const float ri = damping * r[i];
-    for (int32_t k = rowptr[i] + threadIdx.x; k < rowptr[i + 1]; k += blockDim.x) dw[k] = ri * __ldg(&lam[colidx[k]]);
+// dL/dW(i,j) = damping r_i lambda_j over the rows of W: each row block's CTA walks its contiguous
+// entries (coalesced colidx and dW) and finds each entry's row in its staged row pointers
+__global__ void __launch_bounds__(PR_THREADS)
+    pr_edge_grad(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                 const int32_t *__restrict__ blk, const float *__restrict__ r, const float *__restrict__ lam,
+                 float damping, float *__restrict__ dw) {
+  __shared__ int32_t rp[PR_UNITS + 1];
+  const int32_t r0 = blk[blockIdx.x], r1 = blk[blockIdx.x + 1];
+  const int32_t nr = r1 - r0;
+  if (nr == 0) return;
+  for (int32_t q = threadIdx.x; q <= nr; q += PR_THREADS) rp[q] = rowptr[r0 + q];
+  __syncthreads();
+  const int32_t e0 = rp[0], e1 = rp[nr];
+  for (int32_t k = e0 + threadIdx.x; k < e1; k += PR_THREADS) {
+    int32_t lo = 0, hi = nr - 1;  // last q with rp[q] <= k
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (rp[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    dw[k] = damping * r[r0 + lo] * __ldg(&lam[colidx[k]]);
   }
 }
 
@@ -218,64 +305,64 @@ inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
   return (int)b;
 }
 
-inline int pick_group(int64_t nnz, int32_t n) {
-  const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-  if (avg < 6) return 4;
-  if (avg < 12) return 8;
-  if (avg < 24) return 16;
-  return 32;
-}
-
-template <int MODE>
-void launch_rows(int G, int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *val, const float *x,
-                 const float *prev, float *out, float *wout, const float *sc, const float *vvec, float vuni,
-                 const float *gvec, float damping, int dangling, const PrState *st, double2 *partials,
-                 cudaStream_t s) {
-#define LAGR_PR_CASE(GG)                                                                                  \
-  case GG:                                                                                                \
-    pr_rows<GG, MODE><<<PR_BLOCKS, PR_THREADS, 0, s>>>(n, rowptr, colidx, val, x, prev, out, wout, sc, vvec, \
-                                                       vuni, gvec, damping, dangling, st, partials);       \
-    break;
-  switch (G) {
-    LAGR_PR_CASE(4)
-    LAGR_PR_CASE(8)
-    LAGR_PR_CASE(16)
-    default: LAGR_PR_CASE(32)
-  }
-#undef LAGR_PR_CASE
-}
-
 }  // namespace
+
+static inline int heavy_finish_blocks(const RowPlan &pl) {
+  return (pl.nheavy + PR_HF_THREADS - 1) / PR_HF_THREADS;
+}
+
+static inline int n_partials(const RowPlan &pl) {
+  const int np = pl.nblk + heavy_finish_blocks(pl);
+  return np > PR_INIT_BLOCKS ? np : PR_INIT_BLOCKS;
+}
+
+// one iteration: the row-block gather, the heavy rows, the fold of the partials
+template <int MODE>
+static void launch_iter(const RowPlan &pl, const IterArgs &a, PrState *st, double2 *partials, int32_t itermax,
+                        double tol, cudaStream_t s) {
+  pr_stream<MODE><<<pl.nblk + pl.nhc, PR_THREADS, 0, s>>>(a, pl.blk, pl.nblk, pl.heavy, pl.hc_off, pl.hc_row, st,
+                                                           partials);
+  const int hfb = heavy_finish_blocks(pl);
+  if (hfb > 0)
+    pr_heavy_finish<MODE><<<hfb, PR_HF_THREADS, 0, s>>>(a, pl.heavy, pl.nheavy, pl.hc_off, st, partials + pl.nblk);
+  // fold exactly the slots written above (the rest may hold the init kernel's partials)
+  pr_finalize<<<1, 1024, 0, s>>>(partials, pl.nblk + hfb, st, MODE, a.damping, a.dangling, tol, itermax, 0);
+}
+
+// start vector, w0 and the first coefficient (the init partials use the first PR_INIT_BLOCKS slots)
+static void launch_init(int mode, int32_t n, float *x, float *w, const float *sc, const float *src, const float *vvec,
+                        float vuni, PrState *st, double2 *partials, float damping, int dangling, int32_t itermax,
+                        double tol, cudaStream_t s) {
+  if (mode == 2) pr_init<2><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
+  else if (mode == 1) pr_init<1><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
+  else pr_init<0><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, w, sc, src, vvec, vuni, partials);
+  pr_finalize<<<1, 1024, 0, s>>>(partials, PR_INIT_BLOCKS, st, mode, damping, dangling, tol, itermax, 1);
+}
 
 // Run the iteration of `mode` to convergence.  buf0 holds the start vector on entry (MODE 0/1,
 // written here unless warm) and the result on exit.  Returns the iteration count in *iters.
-static int pr_solve(int mode, lagr_graph G, Priv *P, const int32_t *rowptr, const int32_t *colidx, const float *val,
-                    const int32_t *heavy, int32_t nheavy, float *buf0, const float *sc, const float *vvec,
-                    const float *gvec, const float *warm, float damping, float tol, int32_t itermax, int dangling,
-                    PrState *st, int32_t *iters, double *resid, cudaStream_t s, char *msg) {
+static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const int32_t *rowptr, const int32_t *colidx,
+                    const float *val, float *buf0, const float *sc, const float *vvec, const float *gvec,
+                    const float *warm, float damping, float tol, int32_t itermax, int dangling, PrState *st,
+                    int32_t *iters, double *resid, cudaStream_t s, char *msg) {
   const int32_t n = G->n;
-  const int64_t nnz = G->nnz;
-  Temp<float> buf1(s), w0(s), w1(s);
+  Temp<float> buf1(s), w0(s), w1(s), hpart(s);
   Temp<double2> partials(s);
   LAGR_TRY(buf1.alloc(n, msg, "PageRank work vector"));
+  LAGR_TRY(hpart.alloc((size_t)pl.nhc + 1, msg, "heavy chunk sums"));
   if (mode == 0) {
     LAGR_TRY(w0.alloc(n, msg, "PageRank w"));
     LAGR_TRY(w1.alloc(n, msg, "PageRank w"));
   }
-  const int np = PR_BLOCKS + PR_HEAVY_BLOCKS;
+  const int np = n_partials(pl);
   LAGR_TRY(partials.alloc(np, msg, "PageRank partial sums"));
   LAGR_CUDA_TRY(cudaMemsetAsync(partials.p, 0, np * sizeof(double2), s));
   LAGR_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(PrState), s));
   const float vuni = 1.0f / (float)n;
-  const int G_ = pick_group(nnz, n);
   float *x[2] = {buf0, buf1.p};
   float *w[2] = {w0.p, w1.p};
-  // init: the start vector, w0 and the first coefficient
-  const float *src = (mode == 2) ? gvec : warm;
-  if (mode == 2) pr_init<2><<<PR_BLOCKS, PR_THREADS, 0, s>>>(n, buf0, nullptr, sc, src, vvec, vuni, partials.p);
-  else if (mode == 1) pr_init<1><<<PR_BLOCKS, PR_THREADS, 0, s>>>(n, buf0, nullptr, sc, src, vvec, vuni, partials.p);
-  else pr_init<0><<<PR_BLOCKS, PR_THREADS, 0, s>>>(n, buf0, w[0], sc, src, vvec, vuni, partials.p);
-  pr_finalize<<<1, 1024, 0, s>>>(partials.p, np, st, mode, damping, dangling, (double)tol, itermax, 1);
+  launch_init(mode, n, buf0, w[0], sc, (mode == 2) ? gvec : warm, vvec, vuni, st, partials.p, damping, dangling,
+              itermax, (double)tol, s);
   LAGR_LAUNCH_CHECK();
   PrState host{};
   int32_t launched = 0;
@@ -283,33 +370,17 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const int32_t *rowptr, cons
     const int32_t chunk = (itermax - launched < PR_CHUNK) ? (itermax - launched) : PR_CHUNK;
     for (int c = 0; c < chunk; c++) {
       const int k = launched + c + 1;  // iteration number
-      const float *xin = x[(k - 1) & 1];
-      float *xout = x[k & 1];
-      const float *gx = (mode == 0) ? w[(k - 1) & 1] : xin;
-      float *wo = (mode == 0) ? w[k & 1] : nullptr;
+      IterArgs a{rowptr, colidx, val, nullptr, x[(k - 1) & 1], x[k & 1], nullptr, sc, vvec, vuni, gvec, damping,
+                 dangling, hpart.p};
       if (mode == 0) {
-        launch_rows<0>(G_, n, rowptr, colidx, val, gx, xin, xout, wo, sc, vvec, vuni, gvec, damping, dangling, st,
-                       partials.p, s);
-        if (nheavy > 0)
-          pr_rows_heavy<0><<<PR_HEAVY_BLOCKS, 512, 0, s>>>(heavy, nheavy, rowptr, colidx, val, gx, xin, xout, wo, sc,
-                                                          vvec, vuni, gvec, damping, dangling, st,
-                                                          partials.p + PR_BLOCKS);
-      } else if (mode == 1) {
-        launch_rows<1>(G_, n, rowptr, colidx, val, gx, xin, xout, wo, sc, vvec, vuni, gvec, damping, dangling, st,
-                       partials.p, s);
-        if (nheavy > 0)
-          pr_rows_heavy<1><<<PR_HEAVY_BLOCKS, 512, 0, s>>>(heavy, nheavy, rowptr, colidx, val, gx, xin, xout, wo, sc,
-                                                          vvec, vuni, gvec, damping, dangling, st,
-                                                          partials.p + PR_BLOCKS);
+        a.x = w[(k - 1) & 1];
+        a.wout = w[k & 1];
+        launch_iter<0>(pl, a, st, partials.p, itermax, (double)tol, s);
       } else {
-        launch_rows<2>(G_, n, rowptr, colidx, val, gx, xin, xout, wo, sc, vvec, vuni, gvec, damping, dangling, st,
-                       partials.p, s);
-        if (nheavy > 0)
-          pr_rows_heavy<2><<<PR_HEAVY_BLOCKS, 512, 0, s>>>(heavy, nheavy, rowptr, colidx, val, gx, xin, xout, wo, sc,
-                                                          vvec, vuni, gvec, damping, dangling, st,
-                                                          partials.p + PR_BLOCKS);
+        a.x = x[(k - 1) & 1];
+        if (mode == 1) launch_iter<1>(pl, a, st, partials.p, itermax, (double)tol, s);
+        else launch_iter<2>(pl, a, st, partials.p, itermax, (double)tol, s);
       }
-      pr_finalize<<<1, 1024, 0, s>>>(partials.p, np, st, mode, damping, dangling, (double)tol, itermax, 0);
     }
     LAGR_LAUNCH_CHECK();
     launched += chunk;
@@ -350,13 +421,12 @@ static int pr_common_checks(lagr_graph G, float damping, float tol, int32_t iter
 struct PrPlan {
   int32_t n = 0;
   const int32_t *rowptr = nullptr, *colidx = nullptr;
-  const int32_t *heavy = nullptr;
-  int32_t nheavy = 0;
+  RowPlan rows;  // borrowed from the graph's private state
   const float *vvec = nullptr;
   float damping = 0.85f;
-  int G = 32;
-  float *sc = nullptr, *x1 = nullptr, *w0 = nullptr, *w1 = nullptr;
+  float *sc = nullptr, *x1 = nullptr, *w0 = nullptr, *w1 = nullptr, *hpart = nullptr;
   double2 *partials = nullptr;
+  int np = 0;
   PrState *st = nullptr;
 };
 
@@ -364,21 +434,21 @@ int pr_plan_create(PrPlan **out, lagr_graph G, Priv *P, float damping, const flo
                    char *msg) {
   *out = nullptr;
   LAGR_TRY(lagr_property_AT(G, s, msg));
-  if (P->at_nheavy < 0) LAGR_TRY(heavy_rows(G->at_rowptr, G->n, PR_HEAVY, &P->at_heavy, &P->at_nheavy, s, msg));
+  LAGR_TRY(row_plan(&P->pr_at, G->at_rowptr, G->n, s, msg));
   PrPlan *pl = new PrPlan();
   pl->n = G->n;
   pl->rowptr = G->at_rowptr;
   pl->colidx = G->at_colidx;
-  pl->heavy = P->at_heavy;
-  pl->nheavy = P->at_nheavy;
+  pl->rows = P->pr_at;
   pl->vvec = vvec;
   pl->damping = damping;
-  pl->G = pick_group(G->nnz, G->n);
+  pl->np = n_partials(P->pr_at);
   int st = alloc_n(&pl->sc, (size_t)G->n, s, msg, "PageRank scale");
   if (st == LAGR_OK) st = alloc_n(&pl->x1, (size_t)G->n, s, msg, "PageRank work vector");
   if (st == LAGR_OK) st = alloc_n(&pl->w0, (size_t)G->n, s, msg, "PageRank w");
   if (st == LAGR_OK) st = alloc_n(&pl->w1, (size_t)G->n, s, msg, "PageRank w");
-  if (st == LAGR_OK) st = alloc_n(&pl->partials, (size_t)(PR_BLOCKS + PR_HEAVY_BLOCKS), s, msg, "partials");
+  if (st == LAGR_OK) st = alloc_n(&pl->partials, (size_t)pl->np, s, msg, "partials");
+  if (st == LAGR_OK) st = alloc_n(&pl->hpart, (size_t)P->pr_at.nhc + 1, s, msg, "heavy chunk sums");
   if (st == LAGR_OK) st = alloc_n(&pl->st, 1, s, msg, "PageRank state");
   if (st < 0) {
     pr_plan_destroy(pl, s);
@@ -391,23 +461,16 @@ int pr_plan_create(PrPlan **out, lagr_graph G, Priv *P, float damping, const flo
 }
 
 int pr_plan_enqueue(PrPlan *pl, float *out, const float *warm, int32_t iters, cudaStream_t s, char *msg) {
-  const int np = PR_BLOCKS + PR_HEAVY_BLOCKS;
   const float vuni = 1.0f / (float)pl->n;
   float *x[2] = {out, pl->x1};
   float *w[2] = {pl->w0, pl->w1};
-  LAGR_CUDA_TRY(cudaMemsetAsync(pl->partials, 0, np * sizeof(double2), s));
+  LAGR_CUDA_TRY(cudaMemsetAsync(pl->partials, 0, pl->np * sizeof(double2), s));
   LAGR_CUDA_TRY(cudaMemsetAsync(pl->st, 0, sizeof(PrState), s));
-  pr_init<0><<<PR_BLOCKS, PR_THREADS, 0, s>>>(pl->n, out, w[0], pl->sc, warm, pl->vvec, vuni, pl->partials);
-  pr_finalize<<<1, 1024, 0, s>>>(pl->partials, np, pl->st, 0, pl->damping, 0, 0.0, iters, 1);
+  launch_init(0, pl->n, out, w[0], pl->sc, warm, pl->vvec, vuni, pl->st, pl->partials, pl->damping, 0, iters, 0.0, s);
   for (int k = 1; k <= iters; k++) {
-    const float *xin = x[(k - 1) & 1];
-    launch_rows<0>(pl->G, pl->n, pl->rowptr, pl->colidx, nullptr, w[(k - 1) & 1], xin, x[k & 1], w[k & 1], pl->sc,
-                   pl->vvec, vuni, nullptr, pl->damping, 0, pl->st, pl->partials, s);
-    if (pl->nheavy > 0)
-      pr_rows_heavy<0><<<PR_HEAVY_BLOCKS, 512, 0, s>>>(pl->heavy, pl->nheavy, pl->rowptr, pl->colidx, nullptr,
-                                                      w[(k - 1) & 1], xin, x[k & 1], w[k & 1], pl->sc, pl->vvec, vuni,
-                                                      nullptr, pl->damping, 0, pl->st, pl->partials + PR_BLOCKS);
-    pr_finalize<<<1, 1024, 0, s>>>(pl->partials, np, pl->st, 0, pl->damping, 0, 0.0, iters, 0);
+    IterArgs a{pl->rowptr, pl->colidx, nullptr, w[(k - 1) & 1], x[(k - 1) & 1], x[k & 1], w[k & 1], pl->sc,
+               pl->vvec, vuni, nullptr, pl->damping, 0, pl->hpart};
+    launch_iter<0>(pl->rows, a, pl->st, pl->partials, iters, 0.0, s);
   }
   LAGR_LAUNCH_CHECK();
   if (iters & 1)
@@ -422,6 +485,7 @@ void pr_plan_destroy(PrPlan *pl, cudaStream_t s) {
   dev_free(pl->w0, s);
   dev_free(pl->w1, s);
   dev_free(pl->partials, s);
+  dev_free(pl->hpart, s);
   dev_free(pl->st, s);
   delete pl;
 }
@@ -432,11 +496,11 @@ static int pr_forward(float *rank, int32_t *iters, double *resid, lagr_graph G, 
                       int32_t itermax, const float *teleport, int32_t flags, const float *sc, PrState *st,
                       cudaStream_t s, char *msg) {
   LAGR_TRY(lagr_property_AT(G, s, msg));
-  if (P->at_nheavy < 0) LAGR_TRY(heavy_rows(G->at_rowptr, G->n, PR_HEAVY, &P->at_heavy, &P->at_nheavy, s, msg));
+  LAGR_TRY(row_plan(&P->pr_at, G->at_rowptr, G->n, s, msg));
   const int mode = (flags & LAGR_PR_WEIGHTED) ? 1 : 0;
   const float *warm = (flags & LAGR_PR_WARM_START) ? rank : nullptr;
-  return pr_solve(mode, G, P, G->at_rowptr, G->at_colidx, G->at_val, P->at_heavy, P->at_nheavy, rank, sc, teleport,
-                  nullptr, warm, damping, tol, itermax, (flags & LAGR_PR_DANGLING) ? 1 : 0, st, iters, resid, s, msg);
+  return pr_solve(mode, G, P, P->pr_at, G->at_rowptr, G->at_colidx, G->at_val, rank, sc, teleport, nullptr, warm,
+                  damping, tol, itermax, (flags & LAGR_PR_DANGLING) ? 1 : 0, st, iters, resid, s, msg);
 }
 
 }  // namespace lagr
@@ -515,34 +579,25 @@ extern "C" int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t
                         sc.p, st.p, s, msg));
     r = rfwd.p;
   }
-  if (P->a_nheavy < 0) LAGR_TRY(heavy_rows(G->rowptr, G->n, PR_HEAVY, &P->a_heavy, &P->a_nheavy, s, msg));
+  LAGR_TRY(row_plan(&P->pr_a, G->rowptr, G->n, s, msg));
   int32_t k = 0;
   double resid = 0.0;
-  LAGR_TRY(pr_solve(2, G, P, G->rowptr, G->colidx, G->val, P->a_heavy, P->a_nheavy, lam.p, sc.p, teleport,
-                    dL_drank, nullptr, damping, tol, itermax, dangling, st.p, &k, &resid, s, msg));
+  LAGR_TRY(pr_solve(2, G, P, P->pr_a, G->rowptr, G->colidx, G->val, lam.p, sc.p, teleport, dL_drank, nullptr, damping,
+                    tol, itermax, dangling, st.p, &k, &resid, s, msg));
   if (dL_dw && G->nnz > 0) {
-    const int G_ = pick_group(G->nnz, G->n);
-    const int gb = grid_for((int64_t)G->n * G_, 256);
-    switch (G_) {
-      case 4: pr_edge_grad<4><<<gb, 256, 0, s>>>(G->n, G->rowptr, G->colidx, r, lam.p, damping, dL_dw); break;
-      case 8: pr_edge_grad<8><<<gb, 256, 0, s>>>(G->n, G->rowptr, G->colidx, r, lam.p, damping, dL_dw); break;
-      case 16: pr_edge_grad<16><<<gb, 256, 0, s>>>(G->n, G->rowptr, G->colidx, r, lam.p, damping, dL_dw); break;
-      default: pr_edge_grad<32><<<gb, 256, 0, s>>>(G->n, G->rowptr, G->colidx, r, lam.p, damping, dL_dw); break;
-    }
-    if (P->a_nheavy > 0)
-      pr_edge_grad_heavy<<<PR_HEAVY_BLOCKS, 512, 0, s>>>(P->a_heavy, P->a_nheavy, G->rowptr, G->colidx, r, lam.p,
-                                                         damping, dL_dw);
+    // every row, heavy ones included, lies in some block's contiguous entry range
+    pr_edge_grad<<<P->pr_a.nblk, PR_THREADS, 0, s>>>(G->rowptr, G->colidx, P->pr_a.blk, r, lam.p, damping, dL_dw);
     LAGR_LAUNCH_CHECK();
   }
   if (dL_dteleport) {
-    // delta = dangling mass of r, through the init reduction of the forward (aux slot)
+    // delta = dangling mass of r, through the init reduction (aux slot)
     Temp<double2> partials(s);
     Temp<float> scratch(s);
-    LAGR_TRY(partials.alloc(PR_BLOCKS, msg, "partials"));
+    LAGR_TRY(partials.alloc(PR_INIT_BLOCKS, msg, "partials"));
     LAGR_TRY(scratch.alloc(G->n, msg, "scratch"));
-    pr_init<1><<<PR_BLOCKS, PR_THREADS, 0, s>>>(G->n, scratch.p, nullptr, sc.p, r, teleport, 1.0f / (float)G->n,
-                                              partials.p);
-    pr_finalize<<<1, 1024, 0, s>>>(partials.p, PR_BLOCKS, st.p, 1, damping, dangling, 0.0, 1, 1);
+    pr_init<1><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(G->n, scratch.p, nullptr, sc.p, r, teleport, 1.0f / (float)G->n,
+                                                   partials.p);
+    pr_finalize<<<1, 1024, 0, s>>>(partials.p, PR_INIT_BLOCKS, st.p, 1, damping, dangling, 0.0, 1, 1);
     pr_teleport_grad<<<grid_for(G->n, 256), 256, 0, s>>>(G->n, lam.p, st.p, damping, dangling, dL_dteleport);
     LAGR_LAUNCH_CHECK();
   }

@@ -196,6 +196,45 @@ __global__ void gather_transpose(const int32_t *__restrict__ perm, const int32_t
   }
 }
 
+// ---- row plan -----------------------------------------------------------------------------------
+
+__global__ void light_degree(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ ld) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = rowptr[i + 1] - rowptr[i];
+    ld[i] = d <= ROW_HEAVY ? d : 0;
+  }
+}
+
+// blk[b] = first row r with lp[r] + r >= b * ROW_UNITS (lp = exclusive prefix of light degrees)
+__global__ void block_starts(const int32_t *__restrict__ lp, int32_t n, int32_t nblk, int32_t *__restrict__ blk) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nblk; b += (int64_t)gridDim.x * blockDim.x) {
+    if (b == nblk) {
+      blk[b] = n;
+      continue;
+    }
+    const int64_t target = b * (int64_t)ROW_UNITS;
+    int32_t lo = 0, hi = n;  // answer in [lo, hi]
+    while (lo < hi) {
+      const int32_t mid = lo + ((hi - lo) >> 1);
+      if ((int64_t)lp[mid] + mid >= target) hi = mid; else lo = mid + 1;
+    }
+    blk[b] = lo;
+  }
+}
+
+__global__ void heavy_chunk_counts(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ heavy, int32_t nh,
+                                   int32_t *__restrict__ nch) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = rowptr[heavy[h] + 1] - rowptr[heavy[h]];
+    nch[h] = (d + ROW_HCHUNK - 1) / ROW_HCHUNK;
+  }
+}
+
+__global__ void heavy_chunk_rows(const int32_t *__restrict__ hc_off, int32_t nh, int32_t *__restrict__ hc_row) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t c = hc_off[h]; c < hc_off[h + 1]; c++) hc_row[c] = (int32_t)h;
+}
+
 inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -226,19 +265,28 @@ int exclusive_scan(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, c
   return LAGR_OK;
 }
 
+int64_t radix_scratch_len(int64_t n) {
+  const int64_t nblocks = (n + RADIX_TILE - 1) / RADIX_TILE;
+  return 2 * (nblocks * RADIX_BINS + 1);
+}
+
 int radix_sort_pairs(int32_t *keys, int32_t *vals, int32_t *tmp_k, int32_t *tmp_v, int64_t n, int bits,
-                     cudaStream_t s, char *msg) {
+                     cudaStream_t s, char *msg, int32_t *scratch, int64_t *scan_scratch) {
   if (n <= 1) return LAGR_OK;
   const int64_t nblocks = (n + RADIX_TILE - 1) / RADIX_TILE;
-  Temp<int32_t> hist(s), offs(s);
-  LAGR_TRY(hist.alloc(nblocks * RADIX_BINS, msg, "radix histogram"));
-  LAGR_TRY(offs.alloc(nblocks * RADIX_BINS + 1, msg, "radix offsets"));
+  Temp<int32_t> own(s);
+  int32_t *hist = scratch;
+  if (!hist) {
+    LAGR_TRY(own.alloc(radix_scratch_len(n), msg, "radix histogram"));
+    hist = own.p;
+  }
+  int32_t *offs = hist + nblocks * RADIX_BINS + 1;
   int32_t *k_in = keys, *v_in = vals, *k_out = tmp_k, *v_out = tmp_v;
   int passes = 0;
   for (int shift = 0; shift < bits; shift += 8, passes++) {
-    radix_hist<<<(unsigned)nblocks, RADIX_THREADS, 0, s>>>(k_in, n, shift, hist.p, (int)nblocks);
-    LAGR_TRY(exclusive_scan(hist.p, offs.p, nblocks * RADIX_BINS, s, msg));
-    radix_scatter<<<(unsigned)nblocks, RADIX_THREADS, 0, s>>>(k_in, v_in, n, shift, offs.p, (int)nblocks, k_out,
+    radix_hist<<<(unsigned)nblocks, RADIX_THREADS, 0, s>>>(k_in, n, shift, hist, (int)nblocks);
+    LAGR_TRY(exclusive_scan(hist, offs, nblocks * RADIX_BINS, s, msg, scan_scratch));
+    radix_scatter<<<(unsigned)nblocks, RADIX_THREADS, 0, s>>>(k_in, v_in, n, shift, offs, (int)nblocks, k_out,
                                                              v_out);
     LAGR_LAUNCH_CHECK();
     int32_t *t = k_in; k_in = k_out; k_out = t;
@@ -297,6 +345,89 @@ int transpose_csr(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *
   LAGR_TRY(radix_sort_pairs(keys.p, perm.p, tk.p, tv.p, nnz, bits, s, msg));
   gather_transpose<<<grid_for(nnz, 256), 256, 0, s>>>(perm.p, rowid.p, val, nnz, at_colidx, at_val);
   LAGR_LAUNCH_CHECK();
+  return LAGR_OK;
+}
+
+// Build (once) the row plan of a CSR: heavy rows and row blocks.  Synchronises the stream.
+int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg) {
+  if (pl->nblk >= 0) return LAGR_OK;
+  int32_t *heavy = nullptr, nheavy = 0;
+  LAGR_TRY(heavy_rows(rowptr, n, ROW_HEAVY, &heavy, &nheavy, s, msg));
+  Temp<int32_t> ld(s), lp(s);
+  int st = ld.alloc(n, msg, "light degrees");
+  if (st == LAGR_OK) st = lp.alloc((size_t)n + 1, msg, "light prefix");
+  if (st < 0) {
+    dev_free(heavy, s);
+    return st;
+  }
+  light_degree<<<grid_for(n, 256), 256, 0, s>>>(rowptr, n, ld.p);
+  st = exclusive_scan(ld.p, lp.p, n, s, msg);
+  int32_t light = 0;
+  cudaError_t e = cudaGetLastError();
+  if (st == LAGR_OK && e == cudaSuccess) e = cudaMemcpyAsync(&light, lp.p + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (st == LAGR_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (st == LAGR_OK && e != cudaSuccess) {
+    set_msg(msg, "row plan: %s", cudaGetErrorString(e));
+    st = LAGR_ERR_CUDA;
+  }
+  const int64_t nblk = ((int64_t)light + n) / ROW_UNITS + 1;
+  int32_t *blk = nullptr;
+  if (st == LAGR_OK) st = alloc_n(&blk, (size_t)nblk + 1, s, msg, "row blocks");
+  if (st == LAGR_OK) {
+    block_starts<<<grid_for(nblk + 1, 256), 256, 0, s>>>(lp.p, n, (int32_t)nblk, blk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_msg(msg, "row plan: %s", cudaGetErrorString(e));
+      st = LAGR_ERR_CUDA;
+    }
+  }
+  if (st < 0) {
+    dev_free(heavy, s);
+    dev_free(blk, s);
+    return st;
+  }
+  // chunks of the heavy rows
+  int32_t *hc_off = nullptr, *hc_row = nullptr, nhc = 0;
+  if (st == LAGR_OK && nheavy > 0) {
+    Temp<int32_t> nch(s);
+    st = nch.alloc(nheavy, msg, "heavy chunk counts");
+    if (st == LAGR_OK) st = alloc_n(&hc_off, (size_t)nheavy + 1, s, msg, "heavy chunk offsets");
+    if (st == LAGR_OK) {
+      heavy_chunk_counts<<<grid_for(nheavy, 256), 256, 0, s>>>(rowptr, heavy, nheavy, nch.p);
+      st = exclusive_scan(nch.p, hc_off, nheavy, s, msg);
+    }
+    if (st == LAGR_OK) {
+      e = cudaMemcpyAsync(&nhc, hc_off + nheavy, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_msg(msg, "row plan: %s", cudaGetErrorString(e));
+        st = LAGR_ERR_CUDA;
+      }
+    }
+    if (st == LAGR_OK) st = alloc_n(&hc_row, (size_t)nhc, s, msg, "heavy chunk rows");
+    if (st == LAGR_OK) {
+      heavy_chunk_rows<<<grid_for(nheavy, 256), 256, 0, s>>>(hc_off, nheavy, hc_row);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        set_msg(msg, "row plan: %s", cudaGetErrorString(e));
+        st = LAGR_ERR_CUDA;
+      }
+    }
+  }
+  if (st < 0) {
+    dev_free(heavy, s);
+    dev_free(blk, s);
+    dev_free(hc_off, s);
+    dev_free(hc_row, s);
+    return st;
+  }
+  pl->heavy = heavy;
+  pl->nheavy = nheavy;
+  pl->blk = blk;
+  pl->nblk = (int32_t)nblk;
+  pl->hc_off = hc_off;
+  pl->hc_row = hc_row;
+  pl->nhc = nhc;
   return LAGR_OK;
 }
 

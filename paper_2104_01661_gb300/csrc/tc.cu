@@ -22,14 +22,14 @@
 namespace lagr {
 namespace {
 
-constexpr int ORIENT_G = 8;           // lanes per row in the orientation kernels
-constexpr int ORIENT_HEAVY = 2048;    // longer rows are oriented by a whole CTA
 constexpr int TCW_WARPS = 8;          // warps per CTA in the warp-anchor kernel
 constexpr int TCW_SLOTS = 512;        // hash slots per warp
 constexpr int TCW_MAXD = TCW_SLOTS / 2;  // warp anchors: d+ <= wmax <= 256 ...
 constexpr int TCW_MAXDEG = 4096;      // ... and degree <= 4096
 constexpr int TCC_THREADS = 512;      // CTA-anchor kernel
 constexpr int TCC_SLOTS = 8192;       // hash slots per CTA (32 KB); d+ > 4096 uses binary search
+constexpr int TCW_FILTER_BITS_LOG = 11;  // bit filter per warp: 2048 bits
+constexpr int TCC_FILTER_BITS_LOG = 15;  // bit filter per CTA: 32768 bits (4 KB)
 constexpr int TCC_CHUNK = 2048;       // default neighbours per CTA work item
 constexpr int32_t EMPTY = -1;
 
@@ -38,7 +38,6 @@ constexpr int SL_SORT = SC_COUNT0;
 constexpr int SL_DECIDE = SC_COUNT1;
 constexpr int SL_NW = SC_COUNT2;
 constexpr int SL_NC = SC_COUNT3;
-constexpr int SL_NHEAVY = SC_COUNT4;
 constexpr int SL_QW = SC_COUNT5;
 constexpr int SL_QC = SC_COUNT6;
 constexpr int SL_TOTAL = SC_COUNT7;
@@ -67,6 +66,26 @@ __device__ __forceinline__ int hprobe(const int32_t *tab, int logT, int32_t w) {
     h = (h + 1) & mask;
   }
 }
+
+// A set of U(x,:) in shared memory: a bit filter (one bit per hashed value, logM bits wide) in
+// front of an open-addressing table.  Most probes miss (a wedge closes a triangle less than one
+// time in five on the R-MAT graphs), and a miss usually costs one filter word.
+struct HashSet {
+  int32_t *tab;
+  uint32_t *bits;
+  int logT, logM;
+  __device__ __forceinline__ uint32_t fslot(int32_t w) const { return ((uint32_t)w * 0x85EBCA77u) >> (32 - logM); }
+  __device__ __forceinline__ void insert(int32_t w) const {
+    const uint32_t f = fslot(w);
+    atomicOr(&bits[f >> 5], 1u << (f & 31));
+    hinsert(tab, logT, w);
+  }
+  __device__ __forceinline__ int has(int32_t w) const {
+    const uint32_t f = fslot(w);
+    if (!((bits[f >> 5] >> (f & 31)) & 1u)) return 0;
+    return hprobe(tab, logT, w);
+  }
+};
 
 __device__ __forceinline__ int bsearch_has(const int32_t *__restrict__ a, int32_t len, int32_t w) {
   int32_t lo = 0, hi = len;
@@ -112,44 +131,109 @@ __global__ void tc_set_mode(int32_t n, int method, int64_t *__restrict__ dscal) 
 
 // ---- orientation: d+ per vertex, then the oriented rows -------------------------------------------
 
-template <int G>
-__device__ __forceinline__ unsigned group_mask() {
-  if constexpr (G == 32) return LAGR_FULL_MASK;
-  else return ((1u << G) - 1) << ((threadIdx.x & 31) & ~(G - 1));
-}
+// One CTA per row block (see RowPlan): the degrees of the block's neighbours are gathered into
+// shared memory with coalesced colidx loads, then each short row is oriented by one thread and
+// each longer row by one warp.  FILL = false counts d+(v); FILL = true writes U(v,:) in the order
+// of A(v,:) (ballots keep the order inside a warp).  Rows longer than ROW_HEAVY are left to the
+// heavy kernels.
+constexpr int OR_STAGE = ROW_UNITS + ROW_HEAVY + 64;
+constexpr int OR_SHORT = 32;
 
-template <int G>
-__global__ void tc_orient_count(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                const int32_t *__restrict__ deg, int32_t n, int64_t *__restrict__ dscal,
-                                int32_t *__restrict__ dplus, int32_t *__restrict__ heavy) {
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+    tc_orient_rows(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                   const int32_t *__restrict__ deg, const int32_t *__restrict__ blk, int64_t *__restrict__ dscal,
+                   int32_t *__restrict__ dplus, const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx,
+                   int64_t ucap) {
+  __shared__ int32_t stage[OR_STAGE];
+  __shared__ int32_t longrows[ROW_UNITS / (OR_SHORT + 1) + 2];
+  __shared__ int n_long;
   const int sort = (int)dscal[SL_SORT];
-  const int lg = threadIdx.x & (G - 1);
-  const unsigned gm = group_mask<G>();
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
-    const int32_t b = rowptr[v], e = rowptr[v + 1];
-    if (e - b > ORIENT_HEAVY) {
-      if (lg == 0) heavy[atomicAdd((unsigned long long *)&dscal[SL_NHEAVY], 1ull)] = (int32_t)v;
-      continue;
+  const int32_t r0 = blk[blockIdx.x], r1 = blk[blockIdx.x + 1];
+  const int32_t e0 = rowptr[r0], e1 = rowptr[r1];
+  const bool staged = e1 - e0 <= OR_STAGE;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) n_long = 0;
+  if (staged) {
+    int32_t k = e0 + threadIdx.x;
+    for (; k + 3 * 256 < e1; k += 4 * 256) {
+      const int32_t d0 = __ldg(&deg[colidx[k]]);
+      const int32_t d1 = __ldg(&deg[colidx[k + 256]]);
+      const int32_t d2 = __ldg(&deg[colidx[k + 512]]);
+      const int32_t d3 = __ldg(&deg[colidx[k + 768]]);
+      stage[k - e0] = d0;
+      stage[k + 256 - e0] = d1;
+      stage[k + 512 - e0] = d2;
+      stage[k + 768 - e0] = d3;
     }
-    const int32_t dv = e - b;
+    for (; k < e1; k += 256) stage[k - e0] = __ldg(&deg[colidx[k]]);
+  }
+  __syncthreads();
+  auto du_of = [&](int32_t q, int32_t u) { return staged ? stage[q - e0] : __ldg(&deg[u]); };
+  for (int32_t v = r0 + threadIdx.x; v < r1; v += 256) {
+    const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
+    if (dv <= OR_SHORT) {
+      if (FILL) {
+        int64_t out = u_rowptr[v];
+        for (int32_t q = b; q < e; q++) {
+          const int32_t u = colidx[q];
+          if (keep_edge(u, v, du_of(q, u), dv, sort)) {
+            if (out < ucap) u_colidx[out] = u;
+            else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
+            out++;
+          }
+        }
+      } else {
+        int cnt = 0;
+        for (int32_t q = b; q < e; q++) {
+          const int32_t u = colidx[q];
+          cnt += keep_edge(u, v, du_of(q, u), dv, sort);
+        }
+        dplus[v] = cnt;
+      }
+    } else if (dv <= ROW_HEAVY) {
+      longrows[atomicAdd(&n_long, 1)] = v;
+    }
+  }
+  __syncthreads();
+  const unsigned lt = lanemask_lt();
+  for (int q = warp; q < n_long; q += 8) {
+    const int32_t v = longrows[q];
+    const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
+    int64_t out = FILL ? u_rowptr[v] : 0;
     int cnt = 0;
-    for (int32_t k = b + lg; k < e; k += G) {
-      const int32_t u = colidx[k];
-      cnt += keep_edge(u, (int32_t)v, deg[u], dv, sort);
+    for (int32_t base = b; base < e; base += 32) {
+      const int32_t k = base + lane;
+      int32_t u = 0;
+      bool f = false;
+      if (k < e) {
+        u = colidx[k];
+        f = keep_edge(u, v, du_of(k, u), dv, sort);
+      }
+      if (FILL) {
+        const unsigned bal = __ballot_sync(LAGR_FULL_MASK, f);
+        if (f) {
+          const int64_t pos = out + __popc(bal & lt);
+          if (pos < ucap) u_colidx[pos] = u;
+          else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
+        }
+        out += __popc(bal);
+      } else {
+        cnt += f;
+      }
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) cnt += __shfl_xor_sync(gm, cnt, o);
-    if (lg == 0) dplus[v] = cnt;
+    if (!FILL) {
+      cnt = warp_sum(cnt);
+      if (lane == 0) dplus[v] = cnt;
+    }
   }
 }
 
 __global__ void tc_orient_count_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                                       const int32_t *__restrict__ deg, int64_t *__restrict__ dscal,
-                                      int32_t *__restrict__ dplus, const int32_t *__restrict__ heavy) {
+                                      int32_t *__restrict__ dplus, const int32_t *__restrict__ heavy, int32_t nh) {
   __shared__ int red[32];
   const int sort = (int)dscal[SL_SORT];
-  const int64_t nh = dscal[SL_NHEAVY];
   for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
     const int32_t v = heavy[h];
     const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
@@ -163,46 +247,12 @@ __global__ void tc_orient_count_heavy(const int32_t *__restrict__ rowptr, const 
   }
 }
 
-template <int G>
-__global__ void tc_orient_fill(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                               const int32_t *__restrict__ deg, int32_t n, int64_t *__restrict__ dscal,
-                               const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx, int64_t ucap) {
-  const int sort = (int)dscal[SL_SORT];
-  const int lg = threadIdx.x & (G - 1);
-  const unsigned gm = group_mask<G>();
-  const unsigned lt = lanemask_lt();
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
-    const int32_t b = rowptr[v], e = rowptr[v + 1];
-    if (e - b > ORIENT_HEAVY) continue;
-    const int32_t dv = e - b;
-    int64_t out = u_rowptr[v];
-    for (int32_t base = b; base < e; base += G) {
-      const int32_t k = base + lg;
-      int32_t u = 0;
-      bool f = false;
-      if (k < e) {
-        u = colidx[k];
-        f = keep_edge(u, (int32_t)v, deg[u], dv, sort);
-      }
-      const unsigned bal = __ballot_sync(gm, f) & gm;
-      if (f) {
-        const int64_t pos = out + __popc(bal & lt);
-        if (pos < ucap) u_colidx[pos] = u;
-        else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
-      }
-      out += __popc(bal);
-    }
-  }
-}
-
 __global__ void tc_orient_fill_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                                      const int32_t *__restrict__ deg, int64_t *__restrict__ dscal,
                                      const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx,
-                                     int64_t ucap, const int32_t *__restrict__ heavy) {
+                                     int64_t ucap, const int32_t *__restrict__ heavy, int32_t nh) {
   __shared__ int wc[32];
   const int sort = (int)dscal[SL_SORT];
-  const int64_t nh = dscal[SL_NHEAVY];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const unsigned lt = lanemask_lt();
   for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
@@ -276,43 +326,66 @@ __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *_
 
 // ---- intersection counts --------------------------------------------------------------------------
 
-// Walk the neighbours A(x, b..e) in batches of 32; for every neighbour y anchored at x (smaller
-// (d+, id)), probe each element of U(y,:) against x's table.  Warp-collective.
+// One batch of (up to) 32 neighbours A(x, jb..min(jb+32,e)): for every neighbour y anchored at x
+// (smaller (d+, id)), probe each element of U(y,:) against x's set.  Warp-collective.
 template <class Probe>
-__device__ __forceinline__ unsigned long long anchor_batches(int32_t x, int32_t a, int32_t b, int32_t e, int32_t step,
-                                                             const int32_t *__restrict__ colidx,
-                                                             const int32_t *__restrict__ u_rowptr,
-                                                             const int32_t *__restrict__ u_colidx,
-                                                             const int32_t *__restrict__ dplus, Probe &&probe) {
+__device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a, int32_t jb, int32_t e,
+                                                           const int32_t *__restrict__ colidx,
+                                                           const int32_t *__restrict__ u_rowptr,
+                                                           const int32_t *__restrict__ u_colidx,
+                                                           const int32_t *__restrict__ dplus, Probe &&probe) {
   const int lane = threadIdx.x & 31;
   unsigned long long c = 0;
-  for (int32_t jb = b; jb < e; jb += step) {
-    const int32_t j = jb + lane;
-    int32_t st = 0, len = 0;
-    if (j < e) {
-      const int32_t y = colidx[j];
-      const int32_t dy = dplus[y];
-      if (dy > 0 && (dy < a || (dy == a && y < x))) {
-        st = u_rowptr[y];
-        len = dy;
-      }
+  const int32_t j = jb + lane;
+  int32_t st = 0, len = 0;
+  if (j < e) {
+    const int32_t y = colidx[j];
+    const int32_t dy = dplus[y];
+    if (dy > 0 && (dy < a || (dy == a && y < x))) {
+      st = u_rowptr[y];
+      len = dy;
     }
-    warp_segments(st, len, 0, [&](bool valid, int, int, int gidx) {
+  }
+  // lists of 32 or more: the whole warp walks one list at a time.  Shorter lists: when their
+  // lengths are even enough (the longest at most twice the mean), each lane walks its own list;
+  // otherwise the load-balanced walk spreads their elements over the lanes.
+  unsigned longs = __ballot_sync(LAGR_FULL_MASK, len >= 32);
+  const int32_t slen = len >= 32 ? 0 : len;
+  const unsigned total = __reduce_add_sync(LAGR_FULL_MASK, (unsigned)slen);
+  const unsigned lmax = __reduce_max_sync(LAGR_FULL_MASK, (unsigned)slen);
+  if (32u * lmax <= 2u * total) {
+    for (int32_t q = 0; q < slen; q++) c += probe(u_colidx[st + q]);
+  } else if (total > 0) {
+    warp_segments(st, slen, 0, [&](bool valid, int, int, int gidx) {
       if (valid) c += probe(u_colidx[gidx]);
     });
+  }
+  while (longs) {
+    const int sl = __ffs(longs) - 1;
+    longs &= longs - 1;
+    const int32_t st_s = __shfl_sync(LAGR_FULL_MASK, st, sl);
+    const int32_t len_s = __shfl_sync(LAGR_FULL_MASK, len, sl);
+    int32_t k = lane;
+    for (; k + 32 < len_s; k += 64) {
+      const int32_t w0 = u_colidx[st_s + k], w1 = u_colidx[st_s + k + 32];
+      c += probe(w0) + probe(w1);
+    }
+    if (k < len_s) c += probe(u_colidx[st_s + k]);
   }
   return c;
 }
 
-__global__ void __launch_bounds__(TCW_WARPS * 32)
+__global__ void __launch_bounds__(TCW_WARPS * 32, 6)
     tc_count_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                   const int32_t *__restrict__ u_rowptr, const int32_t *__restrict__ u_colidx,
                   const int32_t *__restrict__ dplus, const int32_t *__restrict__ listw, int64_t *__restrict__ dscal,
                   const int32_t *__restrict__ voff, int32_t ngraphs, unsigned long long *__restrict__ counts) {
   __shared__ int32_t tab_all[TCW_WARPS][TCW_SLOTS];
+  __shared__ uint32_t bits_all[TCW_WARPS][(1 << TCW_FILTER_BITS_LOG) / 32];
   __shared__ unsigned long long red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t *tab = tab_all[warp];
+  uint32_t *bits = bits_all[warp];
   const int64_t nw = dscal[SL_NW];
   unsigned long long mine = 0;
   for (;;) {
@@ -322,15 +395,18 @@ __global__ void __launch_bounds__(TCW_WARPS * 32)
     if (it >= nw) break;
     const int32_t x = listw[it];
     const int32_t a = dplus[x];
-    const int logT = ceil_log2(2 * a);
-    const int T = 1 << logT;
+    const HashSet hs{tab, bits, ceil_log2(2 * a), TCW_FILTER_BITS_LOG};
+    const int T = 1 << hs.logT;
     for (int i = lane; i < T; i += 32) tab[i] = EMPTY;
+    for (int i = lane; i < (1 << TCW_FILTER_BITS_LOG) / 32; i += 32) bits[i] = 0u;
     __syncwarp();
     const int32_t ub = u_rowptr[x];
-    for (int i = lane; i < a; i += 32) hinsert(tab, logT, u_colidx[ub + i]);
+    for (int i = lane; i < a; i += 32) hs.insert(u_colidx[ub + i]);
     __syncwarp();
-    unsigned long long c = anchor_batches(x, a, rowptr[x], rowptr[x + 1], 32, colidx, u_rowptr, u_colidx, dplus,
-                                          [&](int32_t w) { return hprobe(tab, logT, w); });
+    unsigned long long c = 0;
+    const int32_t e = rowptr[x + 1];
+    for (int32_t jb = rowptr[x]; jb < e; jb += 32)
+      c += anchor_batch(x, a, jb, e, colidx, u_rowptr, u_colidx, dplus, [&](int32_t w) { return hs.has(w); });
     if (voff) {
       c = warp_sum(c);
       if (lane == 0 && c) atomicAdd(&counts[member_of(voff, ngraphs, x)], c);
@@ -351,14 +427,19 @@ __global__ void __launch_bounds__(TCC_THREADS)
                  const int32_t *__restrict__ dplus, const int2 *__restrict__ listc, int64_t *__restrict__ dscal,
                  const int32_t *__restrict__ voff, int32_t ngraphs, unsigned long long *__restrict__ counts,
                  int chunk, int64_t capc) {
-  extern __shared__ int32_t tab[];
+  extern __shared__ int32_t tab[];  // TCC_SLOTS hash slots, then the bit filter
+  uint32_t *bits = reinterpret_cast<uint32_t *>(tab + TCC_SLOTS);
   __shared__ long long s_it;
+  __shared__ int32_t s_next;  // next neighbour batch of the current item
   __shared__ unsigned long long red[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int64_t nc = min(dscal[SL_NC], capc);  // never read past the list (an overflow sets SC_ERR)
   unsigned long long mine = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QC], 1ull);
+    if (threadIdx.x == 0) {
+      s_it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QC], 1ull);
+      if (s_it < nc) s_next = rowptr[listc[s_it].x] + listc[s_it].y;
+    }
     __syncthreads();
     const long long it = s_it;
     if (it >= nc) break;
@@ -367,23 +448,30 @@ __global__ void __launch_bounds__(TCC_THREADS)
     const int32_t a = dplus[x];
     const int32_t ub = u_rowptr[x];
     const bool hashed = a <= TCC_SLOTS / 2;
-    const int logT = hashed ? ceil_log2(2 * a) : 0;
+    const HashSet hs{tab, bits, hashed ? ceil_log2(2 * a) : 1, TCC_FILTER_BITS_LOG};
     if (hashed) {
-      const int T = 1 << logT;
+      const int T = 1 << hs.logT;
       for (int i = threadIdx.x; i < T; i += blockDim.x) tab[i] = EMPTY;
+      for (int i = threadIdx.x; i < (1 << TCC_FILTER_BITS_LOG) / 32; i += blockDim.x) bits[i] = 0u;
       __syncthreads();
-      for (int i = threadIdx.x; i < a; i += blockDim.x) hinsert(tab, logT, u_colidx[ub + i]);
+      for (int i = threadIdx.x; i < a; i += blockDim.x) hs.insert(u_colidx[ub + i]);
       __syncthreads();
     }
     const int32_t b = rowptr[x] + item.y;
     const int32_t e = min(rowptr[x + 1], b + chunk);
-    unsigned long long c;
-    if (hashed)
-      c = anchor_batches(x, a, b + warp * 32, e, nwarps * 32, colidx, u_rowptr, u_colidx, dplus,
-                         [&](int32_t w) { return hprobe(tab, logT, w); });
-    else
-      c = anchor_batches(x, a, b + warp * 32, e, nwarps * 32, colidx, u_rowptr, u_colidx, dplus,
-                         [&](int32_t w) { return bsearch_has(u_colidx + ub, a, w); });
+    unsigned long long c = 0;
+    // warps take the item's neighbour batches one at a time, so they reach the barrier together
+    for (;;) {
+      int32_t jb = 0;
+      if (lane == 0) jb = atomicAdd(&s_next, 32);
+      jb = __shfl_sync(LAGR_FULL_MASK, jb, 0);
+      if (jb >= e) break;
+      if (hashed)
+        c += anchor_batch(x, a, jb, e, colidx, u_rowptr, u_colidx, dplus, [&](int32_t w) { return hs.has(w); });
+      else
+        c += anchor_batch(x, a, jb, e, colidx, u_rowptr, u_colidx, dplus,
+                          [&](int32_t w) { return bsearch_has(u_colidx + ub, a, w); });
+    }
     if (voff) {
       c = warp_sum(c);
       if (lane == 0 && c) atomicAdd(&counts[member_of(voff, ngraphs, x)], c);
@@ -426,20 +514,20 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
   dev_free(P->tc_dplus, s);
   dev_free(P->tc_listw, s);
   dev_free(P->tc_listc, s);
-  dev_free(P->tc_heavy, s);
   dev_free(P->tc_scan, s);
   P->tc_scan = nullptr;
-  P->tc_dplus = P->tc_listw = P->tc_heavy = nullptr;
+  P->tc_dplus = P->tc_listw = nullptr;
   P->tc_listc = nullptr;
   P->tc_capc = 0;
   G->u_order = -1;
   LAGR_TRY(lagr_property_row_degree(G, s, msg));
+  LAGR_TRY(lagr_property_AT(G, s, msg));  // undirected: A' aliases A, so the row plan is shared
+  LAGR_TRY(row_plan(&P->pr_at, G->rowptr, n, s, msg));
   LAGR_TRY(alloc_n(&P->tc_dplus, (size_t)n + 1, s, msg, "d+"));
   LAGR_TRY(alloc_n(&G->u_rowptr, (size_t)n + 1, s, msg, "U row pointers"));
   LAGR_TRY(alloc_n(&G->u_colidx, (size_t)(nnz / 2 + 1), s, msg, "U column indices"));
   LAGR_TRY(alloc_n(&P->tc_listw, (size_t)n + 1, s, msg, "warp anchors"));
   LAGR_TRY(alloc_n(&P->tc_listc, (size_t)capc, s, msg, "CTA anchors"));
-  LAGR_TRY(alloc_n(&P->tc_heavy, (size_t)(nnz / ORIENT_HEAVY + 1), s, msg, "heavy rows"));
   LAGR_TRY(alloc_n(&P->tc_scan, (size_t)scan_scratch_len(n), s, msg, "scan scratch"));
   P->tc_capc = capc;
   return LAGR_OK;
@@ -460,17 +548,19 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
       tc_decide<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, n, xstar, P->dscal);
     }
     tc_set_mode<<<1, 1, 0, s>>>(n, method, P->dscal);
-    const int ob = grid_for((int64_t)n * ORIENT_G, 256);
-    tc_orient_count<ORIENT_G><<<ob, 256, 0, s>>>(G->rowptr, G->colidx, G->row_degree, n, P->dscal, P->tc_dplus,
-                                                  P->tc_heavy);
-    tc_orient_count_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, G->row_degree, P->dscal, P->tc_dplus,
-                                                  P->tc_heavy);
+    const RowPlan &rp = P->pr_at;
+    tc_orient_rows<false><<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, G->row_degree, rp.blk, P->dscal, P->tc_dplus,
+                                                   nullptr, nullptr, 0);
+    if (rp.nheavy > 0)
+      tc_orient_count_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, G->row_degree, P->dscal, P->tc_dplus,
+                                                    rp.heavy, rp.nheavy);
     LAGR_LAUNCH_CHECK();
     LAGR_TRY(exclusive_scan(P->tc_dplus, G->u_rowptr, n, s, msg, P->tc_scan));
-    tc_orient_fill<ORIENT_G><<<ob, 256, 0, s>>>(G->rowptr, G->colidx, G->row_degree, n, P->dscal, G->u_rowptr,
-                                                 G->u_colidx, ucap);
-    tc_orient_fill_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, G->row_degree, P->dscal, G->u_rowptr,
-                                                 G->u_colidx, ucap, P->tc_heavy);
+    tc_orient_rows<true><<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, G->row_degree, rp.blk, P->dscal, nullptr,
+                                                  G->u_rowptr, G->u_colidx, ucap);
+    if (rp.nheavy > 0)
+      tc_orient_fill_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, G->row_degree, P->dscal, G->u_rowptr,
+                                                   G->u_colidx, ucap, rp.heavy, rp.nheavy);
     tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, P->tc_dplus, n, P->tc_listw, P->tc_listc, P->tc_capc,
                                                  P->dscal, prm.wmax, prm.chunk);
     LAGR_LAUNCH_CHECK();
@@ -480,7 +570,7 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
   }
   if (counts != (unsigned long long *)(P->dscal + SL_TOTAL))
     LAGR_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ngraphs * sizeof(unsigned long long), s));
-  const size_t smem_c = TCC_SLOTS * sizeof(int32_t);
+  const size_t smem_c = TCC_SLOTS * sizeof(int32_t) + (1 << TCC_FILTER_BITS_LOG) / 8;
   LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
   tc_count_cta<<<152 * 4, TCC_THREADS, smem_c, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx, P->tc_dplus,
                                                     P->tc_listc, P->dscal, voff, ngraphs, counts, prm.chunk,
