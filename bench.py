@@ -203,12 +203,16 @@ def run_gpu(args):
         if world > 1:
             torch.distributed.barrier()
         launches0 = L.kernel_launches()
+        L.timing_reset()
+        L.timing_enable(True)
         start.record(stream)
         for k in range(args.steps):
             step(rp, ci, marks[k])
         end.record(stream)
         torch.cuda.synchronize()
+        L.timing_enable(False)
         launches_timed = L.kernel_launches() - launches0
+    ktime = {k: L.timing_read(k) for k in L.TIMED_KERNELS}
     ms_total = max_over_ranks(start.elapsed_time(end), world)
     ms_step = ms_total / args.steps
     tc_ms = statistics.median(m[0].elapsed_time(m[1]) for m in marks)
@@ -277,7 +281,9 @@ def run_gpu(args):
                 "pagerank_gbs_algorithmic": round(pr_gbs, 1),
             },
         }
-        out["roofline"] = roofline(args, n, nnz, iters, pr_ms, hbm_peak, peak_kind)
+        out["kernels"] = {k: {"ms_per_launch": round(ms / c, 4) if c else None, "launches": c}
+                          for k, (ms, c) in ktime.items()}
+        out["roofline"] = roofline(g, ktime, args.steps, hbm_peak, peak_kind, out["components"])
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(g, srcs, budget_s=args.cpu_budget)
         if not args.no_extras and only == "all":
@@ -421,22 +427,63 @@ def extras(L, dev, hbm_peak):
     return res
 
 
-def roofline(args, n, nnz, iters, pr_ms, peak, peak_kind):
-    """Dominant HBM-bound kernel of the step: the PageRank gather iteration.  achieved =
-    algorithmic bytes per iteration / its mean duration (CUDA events around the PageRank call,
-    divided by the iterations run, so launch gaps count against it)."""
-    bytes_iter = 4 * (n + 1) + 4 * nnz + 20 * n
-    ach = bytes_iter * iters / max(pr_ms * 1e-3, 1e-9) / 1e9
+def tc_algorithmic_bytes(g):
+    """Bytes the triangle pass must read at least (one pass over the oriented U):
+    4(n+1) + 4 m_L (the mask rows) + sum over U edges (u,v) of 8 + 4 d+(v) (the row pointer and
+    U(v,:) per edge), U = the neighbours of higher degree rank (ascending (degree, id) order when
+    Alg. 6 sorts, the ids otherwise)."""
+    import numpy as np
+    n = g.n
+    deg = np.diff(g.rowptr).astype(np.int64)
+    sd = np.sort(deg)
+    sort = n > 0 and deg.mean() > 4 * sd[(n - 1) // 2]
+    if sort:
+        rank = np.empty(n, dtype=np.int64)
+        rank[np.lexsort((np.arange(n), deg))] = np.arange(n)
+    else:
+        rank = np.arange(n, dtype=np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int32), deg)
+    cols = g.colidx
+    up = rank[cols] > rank[rows]
+    dplus = np.bincount(rows[up], minlength=n).astype(np.int64)
+    m_l = g.nnz // 2
+    return int(4 * (n + 1) + 4 * m_l + (8 * int(up.sum()) + 4 * int(dplus[cols[up]].sum())))
+
+
+def roofline(g, ktime, steps, peak, peak_kind, comp):
+    """The dominant HBM-bound kernel of the step by device time: the PageRank row-block gather or
+    the triangle pass (its two count kernels).  achieved = algorithmic bytes per launch / the mean
+    launch duration, from CUDA events recorded around every launch in the timed region."""
+    n, nnz = g.n, g.nnz
+    pr_ms, pr_n = ktime["pr_gather"]
+    tc_ms = ktime["tc_count_cta"][0] + ktime["tc_count_warp"][0]
+    tc_n = ktime["tc_count_cta"][1]
+    pr_bytes = 4 * (n + 1) + 4 * nnz + 20 * n
+    cand = []
+    if pr_n:
+        cand.append((pr_ms, "pr_gather (PageRank row-block gather, one iteration)", pr_bytes, pr_ms / pr_n,
+                     "pr_gather_rmat22.json"))
+        comp["pagerank_gather_gbs"] = round(pr_bytes / (pr_ms / pr_n) / 1e6, 1)
+    if tc_n:
+        tc_bytes = tc_algorithmic_bytes(g)
+        cand.append((tc_ms, "tc_count_cta + tc_count_warp (one triangle pass)", tc_bytes, tc_ms / tc_n,
+                     "tc_count_rmat22.json"))
+        comp["tc_count_gbs"] = round(tc_bytes / (tc_ms / tc_n) / 1e6, 1)
+        comp["tc_bytes_per_pass"] = tc_bytes
+    if not cand:
+        return None
+    _, name, nbytes, ms_launch, prof = max(cand)
+    ach = nbytes / (ms_launch * 1e-3) / 1e9
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "pr_rows_rmat22.json")
-    if os.path.exists(prof):
+    path = os.path.join(ROOT, "profiles", prof)
+    if os.path.exists(path):
         try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+            traffic = json.load(open(path)).get("dram_bytes_per_launch")
         except Exception:
             traffic = None
-    return {"kernel": "pr_rows (PageRank gather iteration)", "bound": "hbm", "achieved": round(ach, 1),
-            "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "peak_kind": peak_kind,
-            "bytes_per_launch": bytes_iter, "traffic": traffic}
+    return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "peak_kind": peak_kind, "bytes_per_launch": nbytes,
+            "ms_per_launch": round(ms_launch, 4), "traffic": traffic}
 
 
 # ---------------------------------------------------------------------------------------------

@@ -108,8 +108,11 @@ typedef struct lagr_graph_struct {
   int32_t *row_degree;
 
   /* cached: triangle-counting orientation U (strict upper part after the
-   * optional degree ordering of Alg. 6), held by row, with the original
-   * vertex labels; u_order is the LAGR_TC_* method it was built for. */
+   * optional degree ordering of Alg. 6), held by row: row v (original label)
+   * lists, in the order of A(v,:), the ranks of v's neighbours that rank
+   * above v, a rank being the position in the stable ascending-degree order
+   * (or the label itself when Alg. 6 does not sort).  u_order is the
+   * LAGR_TC_* method it was built for. */
   int32_t *u_rowptr, *u_colidx;
   int64_t u_nnz;
   int32_t u_order;
@@ -301,6 +304,19 @@ const char *lagr_version(void);
 /* Diagnostics: the number of CUDA kernels this library has launched since it was loaded (kernels
  * replayed from a captured CUDA graph are counted once, when captured).  No paper counterpart. */
 uint64_t lagr_kernel_launches(void);
+
+/* Diagnostics: per-kernel device time of the hot kernels (no paper counterpart).
+ * lagr_timing_enable(1) makes every later launch of a timed kernel record a pair of CUDA events
+ * on its launching stream around the launch (not inside CUDA-graph capture); 0 stops it.
+ * lagr_timing_read(name, &ms, &launches) waits for the recorded events of kernel `name`, adds
+ * their durations to the running totals and returns the totals since the last lagr_timing_reset().
+ * Timed names: "pr_gather" (one PageRank / adjoint iteration's row-block gather), "tc_count_cta",
+ * "tc_count_warp" (the masked-product count kernels), "bfs_push_small", "bfs_push_lb", "bfs_pull".
+ * Returns LAGR_ERR_INVALID_VALUE for an unknown name, LAGR_ERR_CUDA if an event failed; the
+ * facility is process-wide and thread-safe, and events hold no device memory of the caller. */
+int lagr_timing_enable(int on);
+int lagr_timing_read(const char *kernel, double *ms, int64_t *launches);
+int lagr_timing_reset(void);
 
 #ifdef __cplusplus
 }

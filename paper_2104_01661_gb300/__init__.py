@@ -93,6 +93,9 @@ _str = ctypes.c_char_p
 _SIGNATURES = {
     "lagr_version": ([], ctypes.c_char_p),
     "lagr_kernel_launches": ([], ctypes.c_uint64),
+    "lagr_timing_enable": ([ctypes.c_int], ctypes.c_int),
+    "lagr_timing_read": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)], ctypes.c_int),
+    "lagr_timing_reset": ([], ctypes.c_int),
     "lagr_set_allocator": ([_vp, _vp, _vp], ctypes.c_int),
     "lagr_graph_new": ([ctypes.POINTER(_G), _i32, _i64, _vp, _vp, _vp, _i32, _str], ctypes.c_int),
     "lagr_graph_free": ([ctypes.POINTER(_G), _vp, _str], ctypes.c_int),
@@ -436,6 +439,30 @@ def pagerank_autograd(rowptr, colidx, w, teleport=None, damping=0.85, tol=1e-7, 
 def kernel_launches() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(load_library().lagr_kernel_launches())
+
+
+TIMED_KERNELS = ("pr_gather", "tc_count_cta", "tc_count_warp", "bfs_push_small", "bfs_push_lb", "bfs_pull")
+
+
+def timing_enable(on: bool = True) -> None:
+    """Record CUDA events around every later launch of the timed hot kernels (or stop)."""
+    load_library().lagr_timing_enable(1 if on else 0)
+
+
+def timing_reset() -> None:
+    rc = load_library().lagr_timing_reset()
+    if rc < 0:
+        raise LagrError(rc, "an event failed", "lagr_timing_reset")
+
+
+def timing_read(kernel: str):
+    """(total device ms, launches) of a timed kernel since the last reset."""
+    ms = ctypes.c_double()
+    cnt = _i64()
+    rc = load_library().lagr_timing_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(cnt))
+    if rc < 0:
+        raise LagrError(rc, f"unknown kernel {kernel!r} or an event failed", "lagr_timing_read")
+    return float(ms.value), int(cnt.value)
 
 
 def version() -> str:

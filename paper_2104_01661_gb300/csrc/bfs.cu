@@ -15,6 +15,7 @@
 // Beamer's rule: pull when the frontier's edges exceed the unexplored edges / alpha, push again
 // when the frontier shrinks below n / beta.
 #include <cstring>
+#include <utility>
 
 #include "internal.cuh"
 
@@ -412,64 +413,257 @@ inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
 }
 
 // ---- 64 sources at once -------------------------------------------------------------------------
+//
+// Bit s of the 64-bit words front[v] / seen[v] belongs to source s.  A level is either a push over
+// the frontier's edges (edge-balanced as above; next bits are OR-ed into acc[v] with a 64-bit
+// atomic, and the touched vertices are finalised afterwards) or a pull over all vertices that some
+// source has not reached yet (coalesced row blocks; a row's scan stops once every source bit it
+// still lacks has been seen among its neighbours).  Either way the level writes level[s][v] for
+// every new bit and the list of vertices of the next frontier.
+
+enum Bfs64Slot { S64_NF = 0, S64_MF = 1, S64_NT = 2, S64_NSLOT = 4 };
 
 __global__ void bfs64_init(int32_t n, int32_t k, int32_t *__restrict__ level, unsigned long long *__restrict__ seen,
-                           unsigned long long *__restrict__ front) {
+                           unsigned long long *__restrict__ fa, unsigned long long *__restrict__ fb,
+                           unsigned long long *__restrict__ acc) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     seen[i] = 0;
-    front[i] = 0;
+    fa[i] = 0;
+    fb[i] = 0;
+    acc[i] = 0;
   }
   const int64_t total = (int64_t)k * n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) level[i] = -1;
 }
 
-__global__ void bfs64_seed(int32_t n, int32_t k, const int32_t *__restrict__ src, int32_t *__restrict__ level,
-                           unsigned long long *__restrict__ seen, unsigned long long *__restrict__ front) {
+__global__ void bfs64_seed(int32_t n, int32_t k, const int32_t *__restrict__ src, const int32_t *__restrict__ rowptr,
+                           int32_t *__restrict__ level, unsigned long long *__restrict__ seen,
+                           unsigned long long *__restrict__ front, int32_t *__restrict__ flist,
+                           int64_t *__restrict__ cnt) {
+  if (threadIdx.x != 0) return;
+  int64_t nf = 0, mf = 0;
+  for (int s = 0; s < k; s++) {
+    const int32_t v = src[s];
+    if (front[v] == 0) {
+      flist[nf++] = v;
+      mf += rowptr[v + 1] - rowptr[v];
+    }
+    seen[v] |= 1ull << s;
+    front[v] |= 1ull << s;
+    level[(int64_t)s * n + v] = 0;
+  }
+  for (int i = 0; i < S64_NSLOT; i++) cnt[i] = 0;
+  cnt[S64_NF] = nf;
+  cnt[S64_MF] = mf;
+}
+
+__device__ __forceinline__ void write_levels(int32_t *__restrict__ level, int32_t n, int32_t v, unsigned long long bits,
+                                             int32_t lev) {
+  while (bits) {
+    const int s = __ffsll((long long)bits) - 1;
+    level[(int64_t)s * n + v] = lev;
+    bits &= bits - 1;
+  }
+}
+
+// append v to a list through a counter (warp-aggregated over the lanes that append)
+__device__ __forceinline__ void list_append(int32_t *__restrict__ list, unsigned long long *counter, int32_t v) {
+  const unsigned act = __activemask();
+  const int leader = __ffs(act) - 1;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(act));
+  base = __shfl_sync(act, base, leader);
+  list[base + __popc(act & lanemask_lt())] = v;
+}
+
+__global__ void bfs64_fdeg(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ flist, int32_t nf,
+                           int32_t *__restrict__ fdeg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x)
+    fdeg[i] = rowptr[flist[i] + 1] - rowptr[flist[i]];
+}
+
+// push: the frontier's edges [b*LB_CHUNK, (b+1)*LB_CHUNK) per CTA; acc[v] |= front[u] & ~seen[v]
+__global__ void __launch_bounds__(256)
+    bfs64_push_lb(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                  const int32_t *__restrict__ flist, int32_t nf, const int32_t *__restrict__ offs,
+                  const unsigned long long *__restrict__ front, const unsigned long long *__restrict__ seen,
+                  unsigned long long *__restrict__ acc, int32_t *__restrict__ touched, int64_t *__restrict__ cnt) {
+  __shared__ int32_t s_off[LB_CHUNK + 1];
+  __shared__ int32_t s_u[LB_CHUNK + 1];
+  __shared__ int32_t s_rs[LB_CHUNK + 1];
+  __shared__ int32_t s_i0, s_cnt;
+  const int32_t total = offs[nf];
+  const int32_t c0 = blockIdx.x * LB_CHUNK;
+  if (c0 >= total) return;
+  const int32_t c1 = min(c0 + LB_CHUNK, total);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < k; s++) {
-      const int32_t v = src[s];
-      seen[v] |= 1ull << s;
-      front[v] |= 1ull << s;
-      level[(int64_t)s * n + v] = 0;
+    int32_t lo = 0, hi = nf - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (offs[mid] <= c0) lo = mid; else hi = mid - 1;
+    }
+    const int32_t i0 = lo;
+    hi = nf - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (offs[mid] <= c1 - 1) lo = mid; else hi = mid - 1;
+    }
+    s_i0 = i0;
+    s_cnt = lo - i0 + 1;
+  }
+  __syncthreads();
+  const int32_t i0 = s_i0, cnt_v = s_cnt;
+  const bool staged = cnt_v <= LB_CHUNK;
+  if (staged) {
+    for (int32_t t = threadIdx.x; t < cnt_v; t += blockDim.x) {
+      const int32_t u = flist[i0 + t];
+      s_off[t] = offs[i0 + t];
+      s_u[t] = u;
+      s_rs[t] = rowptr[u];
+    }
+  }
+  __syncthreads();
+  for (int32_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+    int32_t lo = 0, hi = cnt_v - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if ((staged ? s_off[mid] : offs[i0 + mid]) <= e) lo = mid; else hi = mid - 1;
+    }
+    const int32_t u = staged ? s_u[lo] : flist[i0 + lo];
+    const int32_t rs = staged ? s_rs[lo] : rowptr[u];
+    const int32_t o = staged ? s_off[lo] : offs[i0 + lo];
+    const int32_t v = colidx[rs + (e - o)];
+    const unsigned long long bits = front[u] & ~seen[v];
+    if (bits) {
+      const unsigned long long old = atomicOr(&acc[v], bits);
+      if (old == 0) list_append(touched, (unsigned long long *)&cnt[S64_NT], v);
     }
   }
 }
 
-// next[v] = (OR over in-neighbours u of front[u]) & ~seen[v]; the any/or monoid stops the scan
-// as soon as every still-unseen source bit of v is covered.
-__global__ void __launch_bounds__(BFS_THREADS)
-    bfs64_pull(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t n, int32_t k,
-               unsigned long long kmask, const unsigned long long *__restrict__ front,
-               unsigned long long *__restrict__ next, unsigned long long *__restrict__ seen,
-               int32_t *__restrict__ level, int32_t lev, unsigned long long *__restrict__ newcount) {
-  unsigned long long found = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long sv = seen[v];
-    unsigned long long nw = 0;
-    if (sv != kmask) {
-      unsigned long long acc = 0;
+// after a push: the touched vertices take their new bits
+__global__ void bfs64_finish_push(const int32_t *__restrict__ touched, const int64_t *__restrict__ cnt,
+                                  const int32_t *__restrict__ rowptr, unsigned long long *__restrict__ acc,
+                                  unsigned long long *__restrict__ seen, unsigned long long *__restrict__ fnext,
+                                  int32_t *__restrict__ level, int32_t n, int32_t lev, int32_t *__restrict__ nflist,
+                                  int64_t *__restrict__ out) {
+  const int64_t nt = cnt[S64_NT];
+  unsigned long long mdeg = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = touched[t];
+    const unsigned long long a = acc[v];
+    acc[v] = 0;
+    const unsigned long long nw = a & ~seen[v];
+    if (nw) {
+      seen[v] |= nw;
+      fnext[v] = nw;
+      write_levels(level, n, v, nw, lev);
+      list_append(nflist, (unsigned long long *)&out[S64_NF], v);
+      mdeg += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+    }
+  }
+  mdeg = warp_sum(mdeg);
+  if ((threadIdx.x & 31) == 0 && mdeg) atomicAdd((unsigned long long *)&out[S64_MF], mdeg);
+}
+
+// pull over the row blocks: each vertex still missing some source bit ORs its neighbours' frontier
+// words, stopping once the bits it lacks are all covered.  Short rows: a thread each; longer rows:
+// a warp each; rows longer than ROW_HEAVY: a trailing CTA each.
+__global__ void __launch_bounds__(256)
+    bfs64_pull_rows(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                    const int32_t *__restrict__ blk, int32_t nblk, const int32_t *__restrict__ heavy, int32_t nheavy,
+                    unsigned long long kmask, const unsigned long long *__restrict__ front,
+                    unsigned long long *__restrict__ seen, unsigned long long *__restrict__ fnext,
+                    int32_t *__restrict__ level, int32_t n, int32_t lev, int32_t *__restrict__ nflist,
+                    int64_t *__restrict__ out) {
+  __shared__ int32_t longrows[ROW_UNITS / 33 + 2];
+  __shared__ int n_long;
+  __shared__ unsigned long long s_acc;
+  __shared__ int s_done;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long mdeg = 0;
+  auto settle = [&](int32_t v, unsigned long long sv, unsigned long long acc) {
+    const unsigned long long nw = acc & ~sv;
+    if (nw) {
+      seen[v] = sv | nw;
+      fnext[v] = nw;
+      write_levels(level, n, v, nw, lev);
+      list_append(nflist, (unsigned long long *)&out[S64_NF], v);
+      mdeg += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+    }
+  };
+  if ((int32_t)blockIdx.x >= nblk) {
+    for (int32_t h = blockIdx.x - nblk; h < nheavy; h += gridDim.x - nblk) {
+      const int32_t v = heavy[h];
+      const unsigned long long sv = seen[v];
+      if (sv == kmask) continue;  // uniform: every thread reads the same word
+      if (threadIdx.x == 0) {
+        s_acc = 0;
+        s_done = 0;
+      }
+      __syncthreads();
       const int32_t b = rowptr[v], e = rowptr[v + 1];
+      for (int32_t base = b; base < e; base += blockDim.x) {
+        const int32_t k2 = base + threadIdx.x;
+        unsigned long long x = k2 < e ? __ldg(&front[colidx[k2]]) : 0ull;
+        const unsigned lo = __reduce_or_sync(LAGR_FULL_MASK, (unsigned)x);
+        const unsigned hi = __reduce_or_sync(LAGR_FULL_MASK, (unsigned)(x >> 32));
+        if (lane == 0 && (lo | hi)) atomicOr(&s_acc, ((unsigned long long)hi << 32) | lo);
+        __syncthreads();
+        if (threadIdx.x == 0 && ((s_acc | sv) == kmask)) s_done = 1;
+        __syncthreads();
+        if (s_done) break;
+      }
+      if (threadIdx.x == 0) settle(v, sv, s_acc);
+      __syncthreads();
+    }
+  } else {
+    if (threadIdx.x == 0) n_long = 0;
+    __syncthreads();
+    const int32_t r0 = blk[blockIdx.x], r1 = blk[blockIdx.x + 1];
+    for (int32_t v = r0 + threadIdx.x; v < r1; v += blockDim.x) {
+      const int32_t b = rowptr[v], e = rowptr[v + 1];
+      if (e - b > 32) {
+        if (e - b <= ROW_HEAVY) longrows[atomicAdd(&n_long, 1)] = v;
+        continue;
+      }
+      const unsigned long long sv = seen[v];
+      if (sv == kmask) continue;
+      unsigned long long acc = 0;
       for (int32_t q = b; q < e; q++) {
         acc |= __ldg(&front[colidx[q]]);
         if ((acc | sv) == kmask) break;
       }
-      nw = acc & ~sv;
-      if (nw) {
-        seen[v] = sv | nw;
-        found++;
-        unsigned long long bits = nw;
-        while (bits) {
-          const int s = __ffsll((long long)bits) - 1;
-          level[(int64_t)s * n + v] = lev;
-          bits &= bits - 1;
-        }
-      }
+      settle(v, sv, acc);
     }
-    next[v] = nw;
+    __syncthreads();
+    for (int q = warp; q < n_long; q += 8) {
+      const int32_t v = longrows[q];
+      const unsigned long long sv = seen[v];
+      if (sv == kmask) continue;
+      const int32_t b = rowptr[v], e = rowptr[v + 1];
+      unsigned long long acc = 0;
+      for (int32_t base = b; base < e; base += 32) {
+        const int32_t k2 = base + lane;
+        const unsigned long long x = k2 < e ? __ldg(&front[colidx[k2]]) : 0ull;
+        const unsigned lo = __reduce_or_sync(LAGR_FULL_MASK, (unsigned)x);
+        const unsigned hi = __reduce_or_sync(LAGR_FULL_MASK, (unsigned)(x >> 32));
+        acc |= ((unsigned long long)hi << 32) | lo;
+        if ((acc | sv) == kmask) break;
+      }
+      if (lane == 0) settle(v, sv, acc);
+    }
   }
-  found = warp_sum(found);
-  if ((threadIdx.x & 31) == 0 && found) atomicAdd(newcount, found);
+  mdeg = warp_sum(mdeg);
+  if (lane == 0 && mdeg) atomicAdd((unsigned long long *)&out[S64_MF], mdeg);
+}
+
+// the old frontier's words go back to zero, so the buffer can hold the level after next
+__global__ void bfs64_clear(const int32_t *__restrict__ flist, int32_t nf, unsigned long long *__restrict__ front) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x)
+    front[flist[i]] = 0;
 }
 
 }  // namespace
@@ -552,8 +746,11 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
       if (nq <= SMALL_MAX && mf <= SMALL_EDGES) {
         // several narrow levels in one CTA; it stops when the frontier empties, widens, or the
         // direction rule asks for a pull (the same rule as above, so it runs at least one level)
-        bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level, parent, cnt.p,
-                                                   n, push_only ? 0 : 1);
+        {
+          KTimer kt(TK_BFS_SMALL, s);
+          bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level, parent,
+                                                     cnt.p, n, push_only ? 0 : 1);
+        }
         LAGR_LAUNCH_CHECK();
         LAGR_TRY(sync_counters());
         const int32_t done = (int32_t)h[B_LEV] - lev;
@@ -575,8 +772,11 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
         LAGR_TRY(exclusive_scan(fdeg.p, offs.p, nq, s, msg));
         LAGR_CUDA_TRY(cudaMemsetAsync(nbits.p, 0, nwords * sizeof(uint32_t), s));
         const int64_t nchunks = (mf + LB_CHUNK - 1) / LB_CHUNK;
-        bfs_push_lb<<<(unsigned)(nchunks > 0 ? nchunks : 1), 256, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, offs.p,
-                                                                         visited.p, nbits.p, level, parent, cnt.p);
+        {
+          KTimer kt(TK_BFS_LB, s);
+          bfs_push_lb<<<(unsigned)(nchunks > 0 ? nchunks : 1), 256, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, offs.p,
+                                                                           visited.p, nbits.p, level, parent, cnt.p);
+        }
         bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0);
         LAGR_LAUNCH_CHECK();
         uint32_t *t = fbits.p;
@@ -596,9 +796,12 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
       LAGR_LAUNCH_CHECK();
       rep = 1;
     }
-    bfs_pull<<<grid_for(nwords * 32, BFS_THREADS), BFS_THREADS, 0, s>>>(G->at_rowptr, G->at_colidx, G->rowptr, n,
-                                                                        fbits.p, nbits.p, visited.p, level, parent,
-                                                                        cnt.p);
+    {
+      KTimer kt(TK_BFS_PULL, s);
+      bfs_pull<<<grid_for(nwords * 32, BFS_THREADS), BFS_THREADS, 0, s>>>(G->at_rowptr, G->at_colidx, G->rowptr, n,
+                                                                          fbits.p, nbits.p, visited.p, level, parent,
+                                                                          cnt.p);
+    }
     bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0);
     LAGR_LAUNCH_CHECK();
     {
@@ -641,39 +844,71 @@ extern "C" int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src
   cudaStream_t s = (cudaStream_t)stream;
   Priv *P = nullptr;
   LAGR_TRY(priv_get(G, s, msg, &P));
+  LAGR_TRY(lagr_property_AT(G, s, msg));
+  LAGR_TRY(row_plan(&P->pr_at, G->rowptr, G->n, s, msg));
+  const RowPlan &rp = P->pr_at;
   const int32_t n = G->n;
-  Temp<unsigned long long> seen(s), fa(s), fb(s), cnt(s);
-  Temp<int32_t> dsrc(s);
-  LAGR_TRY(seen.alloc(n, msg, "seen bitmap"));
+  Temp<unsigned long long> seen(s), fa(s), fb(s), acc(s);
+  Temp<int32_t> dsrc(s), la(s), lb(s), touched(s), fdeg(s), offs(s);
+  Temp<int64_t> cnt(s);
+  LAGR_TRY(seen.alloc(n, msg, "seen words"));
   LAGR_TRY(fa.alloc(n, msg, "frontier words"));
   LAGR_TRY(fb.alloc(n, msg, "frontier words"));
-  LAGR_TRY(cnt.alloc(1, msg, "counter"));
+  LAGR_TRY(acc.alloc(n, msg, "push words"));
   LAGR_TRY(dsrc.alloc(k, msg, "sources"));
+  LAGR_TRY(la.alloc(n, msg, "frontier list"));
+  LAGR_TRY(lb.alloc(n, msg, "frontier list"));
+  LAGR_TRY(touched.alloc(n, msg, "touched list"));
+  LAGR_TRY(fdeg.alloc(n, msg, "frontier degrees"));
+  LAGR_TRY(offs.alloc((size_t)n + 1, msg, "frontier offsets"));
+  LAGR_TRY(cnt.alloc(2 * S64_NSLOT, msg, "counters"));
   // the sources travel through the pinned mirror so the copy is asynchronous
   memcpy(P->hscal, src, (size_t)k * sizeof(int32_t));
   LAGR_CUDA_TRY(cudaMemcpyAsync(dsrc.p, P->hscal, (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   const unsigned long long kmask = (k == 64) ? ~0ull : ((1ull << k) - 1);
-  bfs64_init<<<grid_for((int64_t)k * n, 256), 256, 0, s>>>(n, k, level, seen.p, fa.p);
-  bfs64_seed<<<1, 32, 0, s>>>(n, k, dsrc.p, level, seen.p, fa.p);
+  bfs64_init<<<grid_for((int64_t)k * n, 256), 256, 0, s>>>(n, k, level, seen.p, fa.p, fb.p, acc.p);
+  bfs64_seed<<<1, 32, 0, s>>>(n, k, dsrc.p, G->rowptr, level, seen.p, fa.p, la.p, cnt.p);
   LAGR_LAUNCH_CHECK();
-  unsigned long long *front = fa.p, *next = fb.p;
+  unsigned long long *front = fa.p, *fnext = fb.p;
+  int32_t *flist = la.p, *nflist = lb.p;
+  int64_t *cur = cnt.p, *nxt = cnt.p + S64_NSLOT;  // counters of this level / the next
+  LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, cur, S64_NSLOT * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  int64_t nf = P->hscal[S64_NF], mf = P->hscal[S64_MF];
   int32_t lev = 0;
-  for (;;) {
+  const int nhb = rp.nheavy < 152 ? rp.nheavy : 152;
+  while (nf > 0) {
     lev++;
     if (lev > n) {
       set_msg(msg, "BFS exceeded n levels");
       return LAGR_ERR_TIMEOUT;
     }
-    LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
-    bfs64_pull<<<grid_for(n, BFS_THREADS), BFS_THREADS, 0, s>>>(G->rowptr, G->colidx, n, k, kmask, front, next, seen.p,
-                                                               level, lev, cnt.p);
+    LAGR_CUDA_TRY(cudaMemsetAsync(nxt, 0, S64_NSLOT * sizeof(int64_t), s));
+    if (mf * ALPHA_DO < G->nnz) {
+      // push over the frontier's edges
+      bfs64_fdeg<<<grid_for(nf, 256), 256, 0, s>>>(G->rowptr, flist, (int32_t)nf, fdeg.p);
+      LAGR_LAUNCH_CHECK();
+      LAGR_TRY(exclusive_scan(fdeg.p, offs.p, nf, s, msg));
+      LAGR_CUDA_TRY(cudaMemsetAsync(cur + S64_NT, 0, sizeof(int64_t), s));
+      const int64_t nchunks = (mf + LB_CHUNK - 1) / LB_CHUNK;
+      if (nchunks > 0)
+        bfs64_push_lb<<<(unsigned)nchunks, 256, 0, s>>>(G->rowptr, G->colidx, flist, (int32_t)nf, offs.p, front,
+                                                        seen.p, acc.p, touched.p, cur);
+      bfs64_finish_push<<<grid_for(n, 256), 256, 0, s>>>(touched.p, cur, G->rowptr, acc.p, seen.p, fnext, level, n,
+                                                         lev, nflist, nxt);
+    } else {
+      bfs64_pull_rows<<<rp.nblk + nhb, 256, 0, s>>>(G->rowptr, G->colidx, rp.blk, rp.nblk, rp.heavy, rp.nheavy, kmask,
+                                                    front, seen.p, fnext, level, n, lev, nflist, nxt);
+    }
+    bfs64_clear<<<grid_for(nf, 256), 256, 0, s>>>(flist, (int32_t)nf, front);
     LAGR_LAUNCH_CHECK();
-    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, cnt.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, nxt, S64_NSLOT * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     LAGR_CUDA_TRY(cudaStreamSynchronize(s));
-    if (P->hscal[0] == 0) break;
-    unsigned long long *t = front;
-    front = next;
-    next = t;
+    nf = P->hscal[S64_NF];
+    mf = P->hscal[S64_MF];
+    std::swap(front, fnext);
+    std::swap(flist, nflist);
+    std::swap(cur, nxt);
   }
   G->last_levels = lev;
   clear_msg(msg);

@@ -3,6 +3,9 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <mutex>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace lagr {
@@ -82,12 +85,15 @@ int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out) {
 static void free_tc_cache(Priv *P, cudaStream_t s) {
   dev_free(P->tc_dplus, s);
   dev_free(P->tc_listw, s);
+  dev_free(P->tc_listwh, s);
   dev_free(P->tc_listc, s);
   dev_free(P->tc_scan, s);
   dev_free(P->tc_rank, s);
   dev_free(P->tc_sortbuf, s);
   dev_free(P->tc_radix, s);
   dev_free(P->tc_radix_scan, s);
+  P->tc_listwh = nullptr;
+  P->tc_capwh = 0;
   P->tc_rank = P->tc_sortbuf = P->tc_radix = nullptr;
   P->tc_radix_scan = nullptr;
   P->tc_scan = nullptr;
@@ -106,6 +112,7 @@ void priv_release(lagr_graph G, cudaStream_t s) {
     dev_free(rp->heavy, s);
     dev_free(rp->hc_off, s);
     dev_free(rp->hc_row, s);
+    dev_free(rp->hblk, s);
   }
   dev_free(P->dscal, s);
   if (P->hscal) {
@@ -202,11 +209,103 @@ inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
 
 using namespace lagr;
 
+// ---- opt-in kernel timing -----------------------------------------------------------------------
+
+namespace lagr {
+static const char *const kTimedNames[TK_COUNT] = {"pr_gather",      "tc_count_cta", "tc_count_warp",
+                                                  "bfs_push_small", "bfs_push_lb",  "bfs_pull"};
+struct TimedPair {
+  int k;
+  cudaEvent_t a, b;
+};
+static std::mutex g_tmu;
+static int g_timing = 0;
+static std::vector<TimedPair> g_pending;
+static double g_tms[TK_COUNT];
+static int64_t g_tcount[TK_COUNT];
+
+KTimer::KTimer(TimedKernel k_, cudaStream_t s_) : k(k_), s(s_) {
+  if (!__atomic_load_n(&g_timing, __ATOMIC_RELAXED)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess ||
+      cudaEventRecord(a, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    a = b = nullptr;
+  }
+}
+
+KTimer::~KTimer() {
+  if (!a) return;
+  if (cudaEventRecord(b, s) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_pending.push_back(TimedPair{(int)k, a, b});
+}
+
+// fold the recorded pairs into the totals (waits for them)
+static int timing_collect() {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  int rc = LAGR_OK;
+  for (const TimedPair &p : g_pending) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_tms[p.k] += ms;
+      g_tcount[p.k] += 1;
+    } else {
+      cudaGetLastError();
+      rc = LAGR_ERR_CUDA;
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_pending.clear();
+  return rc;
+}
+}  // namespace lagr
+
 extern "C" {
 
 const char *lagr_version(void) { return "lagr-gb300 0.1 (sm_103a)"; }
 
 uint64_t lagr_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+
+int lagr_timing_enable(int on) {
+  __atomic_store_n(&lagr::g_timing, on ? 1 : 0, __ATOMIC_RELAXED);
+  return LAGR_OK;
+}
+
+int lagr_timing_reset(void) {
+  const int rc = lagr::timing_collect();
+  std::lock_guard<std::mutex> lk(lagr::g_tmu);
+  for (int k = 0; k < lagr::TK_COUNT; k++) {
+    lagr::g_tms[k] = 0.0;
+    lagr::g_tcount[k] = 0;
+  }
+  return rc;
+}
+
+int lagr_timing_read(const char *kernel, double *ms, int64_t *launches) {
+  if (!kernel || !ms || !launches) return LAGR_ERR_NULL_POINTER;
+  int k = 0;
+  while (k < lagr::TK_COUNT && strcmp(kernel, lagr::kTimedNames[k]) != 0) k++;
+  if (k == lagr::TK_COUNT) return LAGR_ERR_INVALID_VALUE;
+  const int rc = lagr::timing_collect();
+  std::lock_guard<std::mutex> lk(lagr::g_tmu);
+  *ms = lagr::g_tms[k];
+  *launches = lagr::g_tcount[k];
+  return rc;
+}
 
 int lagr_set_allocator(lagr_alloc_fn alloc, lagr_free_fn free_, void *ctx) {
   if ((alloc == nullptr) != (free_ == nullptr)) return LAGR_ERR_NULL_POINTER;

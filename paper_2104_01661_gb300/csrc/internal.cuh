@@ -82,9 +82,9 @@ struct Temp {
 
 // Partition of the rows of a CSR for the row-block kernels (PageRank gathers, the triangle-count
 // orientation): rows of at most ROW_HEAVY entries are grouped into blocks of at most ROW_UNITS
-// units (a unit is one entry or one row), one CTA each; longer rows are listed in `heavy`
-// (ascending) and handled by a CTA each.  A block's entries are contiguous, at most
-// ROW_UNITS + ROW_HEAVY of them unless the block holds a heavy row.
+// units (a unit is one entry or one row); longer rows are listed in `heavy` (ascending), each a
+// block of its own, and handled by CTAs of their own.  A block's entries are contiguous, at most
+// ROW_UNITS + ROW_HEAVY of them unless the block is a heavy row.
 constexpr int ROW_UNITS = 4096;
 constexpr int ROW_HEAVY = 4096;
 struct RowPlan {
@@ -97,6 +97,7 @@ struct RowPlan {
   int32_t *hc_off = nullptr;  // [nheavy + 1]
   int32_t *hc_row = nullptr;  // [nhc]
   int32_t nhc = 0;
+  uint8_t *hblk = nullptr;    // [nblk] 1 where the block is one heavy row (every heavy row is a block of its own)
 };
 constexpr int ROW_HCHUNK = 8192;
 
@@ -114,6 +115,8 @@ struct Priv {
   int64_t *tc_radix_scan = nullptr;
   int64_t *tc_scan = nullptr;
   int64_t tc_capc = 0;
+  int2 *tc_listwh = nullptr;  // warp items of the warp anchors with many neighbours
+  int64_t tc_capwh = 0;
   // row plans of the PageRank gathers over the rows of A' (forward) and of A (adjoint)
   RowPlan pr_at, pr_a;
 };
@@ -128,6 +131,7 @@ enum ScalarSlot {
   SC_COUNT5 = 6,
   SC_COUNT6 = 7,
   SC_COUNT7 = 8,
+  SC_COUNT8 = 9,
   LAGR_NSCAL = 16,
   LAGR_NHOST = 64  // int64 slots of the pinned host mirror (also stages up to 64 int32 sources)
 };
@@ -136,6 +140,20 @@ int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out);
 
 // build (once; no-op when pl->nblk >= 0) the row plan of a CSR.  Synchronises the stream.
 int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg);
+
+// Opt-in device timing of the hot kernels (lagr_timing_*): construct a KTimer right before a
+// launch and let it go out of scope right after; it records an event pair on the stream when
+// timing is on and the stream is not capturing.
+enum TimedKernel { TK_PR_GATHER = 0, TK_TC_CTA, TK_TC_WARP, TK_BFS_SMALL, TK_BFS_LB, TK_BFS_PULL, TK_COUNT };
+struct KTimer {
+  KTimer(TimedKernel k, cudaStream_t s);
+  ~KTimer();
+  KTimer(const KTimer &) = delete;
+  KTimer &operator=(const KTimer &) = delete;
+  TimedKernel k;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
 void priv_release(lagr_graph G, cudaStream_t s);
 
 // validation shared by the entry points

@@ -5,16 +5,16 @@
 // w = damping * r / d_out (eWiseMult), and per-CTA partial sums of |t - r| (the apply(abs) +
 // reduce of the stopping test) and of the dangling mass.
 //
-// Work partition (a RowPlan, built once per graph and cached): rows of at most PR_HEAVY entries
+// Work partition (a RowPlan, built once per graph and cached): rows of at most ROW_HEAVY entries
 // are grouped into blocks of at most PR_UNITS units, a unit being one entry or one row (so long
-// runs of isolated vertices cannot pile up in one block).  A block's entries are contiguous in
-// the CSR, so its CTA loads colidx fully coalesced and keeps many independent gathers x[colidx]
-// in flight, staging the gathered values in shared memory; each short row is then summed by one
-// thread and each longer row by one warp, in a fixed order (deterministic results).  Rows longer
-// than PR_HEAVY are cut into fixed chunks, summed by trailing CTAs of the same launch, and a small
-// kernel adds each such row's chunk sums in chunk order.  A one-block kernel folds the per-CTA partials in a
-// fixed order, decides convergence on the device and prepares the next iteration's scalar; later
-// launches of the same batch see the flag and return at once.
+// runs of isolated vertices cannot pile up in one block).  One warp sums one block: its entries
+// are contiguous in the CSR, so the warp reads colidx in coalesced steps and keeps a step's
+// gathers x[colidx] in flight together; rows are joined across lanes by a segmented scan, in a
+// fixed order (deterministic results).  Rows longer than ROW_HEAVY are cut into fixed chunks,
+// summed by trailing CTAs of the same launch, and a small kernel adds each such row's chunk sums
+// in chunk order.  A one-block kernel folds the per-block partials in a fixed order, decides
+// convergence on the device and prepares the next iteration's scalar; later launches of the same
+// batch see the flag and return at once.
 //
 // MODE 0: unweighted forward    r_i  = v_i c + sum_{j in A'(i,:)} w_j,   w_j = damping t_j / d_out(j)
 // MODE 1: weighted forward      r_i  = v_i c + damping sum_j W(j,i) t_j
@@ -30,9 +30,6 @@ namespace {
 
 constexpr int PR_THREADS = 256;
 constexpr int PR_UNITS = ROW_UNITS;                 // units (entries + rows) per row block
-constexpr int PR_HEAVY = ROW_HEAVY;                 // longer rows: one CTA each
-constexpr int PR_STAGE = PR_UNITS + PR_HEAVY + 64;  // staged values per block (bound + slack)
-constexpr int PR_SHORT = 32;                        // rows up to this length: one thread each
 constexpr int PR_CHUNK = 8;                         // iterations launched between host checks
 constexpr int PR_INIT_BLOCKS = 152 * 8;
 
@@ -88,6 +85,7 @@ struct IterArgs {
   float damping;
   int dangling;
   float *hpart;       // partial sums of the heavy-row chunks
+  int vec;            // colidx (and val) are 16-byte aligned: steps load them as vectors
 };
 
 template <int MODE>
@@ -118,23 +116,72 @@ __device__ __forceinline__ void row_out(const IterArgs &a, int32_t i, float acc,
   else if (s == 0.0f) aux += (double)r;
 }
 
-// one CTA per row block
+// ---- one warp per row block ----------------------------------------------------------------------
+//
+// A warp walks its block's entries in steps of 32 x PR_EPL: lane l takes the PR_EPL consecutive
+// entries at step_start + PR_EPL * l (colidx read as 16-byte vectors where aligned, so a step is one
+// contiguous, coalesced read), issues all their gathers, then adds them up in entry order, closing
+// a row whenever its end passes.  A row that runs over lane (or step) boundaries is joined by one
+// segmented scan over the lanes per step: lane l contributes the open part of its last row, and the
+// lane where the row ends adds the joined prefix to its own part.  The next step's column indices
+// are loaded while the current step is summed.  Sums are in a fixed order (deterministic).
+// Empty rows are written by a separate pass over the block's rows.  A row longer than ROW_HEAVY is
+// a block of its own, skipped here (its chunks are summed by the trailing CTAs).
+
+constexpr int PR_EPL = 8;                  // entries per lane per step
+constexpr int PR_STEP = 32 * PR_EPL;       // entries per warp step
+constexpr int PR_WARPS = PR_THREADS / 32;  // row blocks per CTA
+
+// the column indices (and values) of entries k .. k + PR_EPL - 1; those outside [lo, hi) read as -1
+template <int MODE>
+__device__ __forceinline__ void load_step(const IterArgs &a, int32_t k, int32_t lo, int32_t hi, int32_t (&c)[PR_EPL],
+                                          float (&v)[PR_EPL]) {
+  if (a.vec && k >= 0 && k + PR_EPL <= hi) {
+    const int4 c0 = __ldg(reinterpret_cast<const int4 *>(a.colidx + k));
+    const int4 c1 = __ldg(reinterpret_cast<const int4 *>(a.colidx + k + 4));
+    c[0] = c0.x; c[1] = c0.y; c[2] = c0.z; c[3] = c0.w;
+    c[4] = c1.x; c[5] = c1.y; c[6] = c1.z; c[7] = c1.w;
+    if (MODE != 0) {
+      const float4 v0 = __ldg(reinterpret_cast<const float4 *>(a.val + k));
+      const float4 v1 = __ldg(reinterpret_cast<const float4 *>(a.val + k + 4));
+      v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w;
+      v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
+    }
+#pragma unroll
+    for (int j = 0; j < PR_EPL; j++)
+      if (k + j < lo) c[j] = -1;
+  } else {
+#pragma unroll
+    for (int j = 0; j < PR_EPL; j++) {
+      const bool ok = k + j >= lo && k + j < hi;
+      c[j] = ok ? __ldg(a.colidx + k + j) : -1;
+      if (MODE != 0) v[j] = ok ? __ldg(a.val + k + j) : 0.0f;
+    }
+  }
+}
+
+// last row i in [lo, hi] with rowptr[i] <= k (rowptr[lo] <= k holds)
+__device__ __forceinline__ int32_t row_of(const int32_t *__restrict__ rowptr, int32_t lo, int32_t hi, int32_t k) {
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(rowptr + mid) <= k) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(PR_THREADS)
-    pr_stream(IterArgs a, const int32_t *__restrict__ blk, int32_t nblk, const int32_t *__restrict__ heavy,
-              const int32_t *__restrict__ hc_off, const int32_t *__restrict__ hc_row, const PrState *__restrict__ st,
-              double2 *__restrict__ partials) {
-  __shared__ float stage[PR_STAGE];
-  // a row longer than PR_SHORT spends more than PR_SHORT + 1 of the block's PR_UNITS units
-  __shared__ int32_t longrows[PR_UNITS / (PR_SHORT + 1) + 2];
-  __shared__ int n_long;
-  __shared__ double red[32];
+    pr_warp(IterArgs a, const int32_t *__restrict__ blk, int32_t nblk, const uint8_t *__restrict__ hblk,
+            const int32_t *__restrict__ heavy, const int32_t *__restrict__ hc_off, const int32_t *__restrict__ hc_row,
+            const PrState *__restrict__ st, double2 *__restrict__ partials) {
+  __shared__ float red[32];
   if (st->done) return;  // uniform over the grid
   const float coef = st->coef;
-  if ((int32_t)blockIdx.x >= nblk) {
-    // the trailing CTAs each sum one chunk of ROW_HCHUNK entries of a row longer than PR_HEAVY,
+  const int32_t nwb = (nblk + PR_WARPS - 1) / PR_WARPS;  // CTAs of row blocks
+  if ((int32_t)blockIdx.x >= nwb) {
+    // the trailing CTAs each sum one chunk of ROW_HCHUNK entries of a row longer than ROW_HEAVY,
     // while the row blocks are still being processed; pr_heavy_finish adds the chunks up
-    const int32_t cidx = blockIdx.x - nblk;
+    const int32_t cidx = blockIdx.x - nwb;
     const int32_t h = hc_row[cidx];
     const int32_t i = heavy[h];
     const int32_t b = a.rowptr[i] + (cidx - hc_off[h]) * ROW_HCHUNK;
@@ -147,80 +194,112 @@ __global__ void __launch_bounds__(PR_THREADS)
       acc += (g0 + g1) + (g2 + g3);
     }
     for (; k < e; k += PR_THREADS) acc += gather_one<MODE>(a, k);
-    acc = block_sum(acc, reinterpret_cast<float *>(stage));
+    acc = block_sum(acc, red);
     if (threadIdx.x == 0) a.hpart[cidx] = acc;
     return;
   }
-  const int32_t r0 = blk[blockIdx.x], r1 = blk[blockIdx.x + 1];
+  const int lane = threadIdx.x & 31;
+  const int32_t wb = blockIdx.x * PR_WARPS + (threadIdx.x >> 5);
+  if (wb >= nblk) return;
+  const int32_t r0 = blk[wb], r1 = blk[wb + 1];
+  const int32_t *__restrict__ rowptr = a.rowptr;
   double resid = 0.0, aux = 0.0;
-  if (threadIdx.x == 0) n_long = 0;
-  const int32_t e0 = a.rowptr[r0], e1 = a.rowptr[r1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (e1 - e0 <= PR_STAGE) {
-    // stage the gathered values of the whole block: colidx coalesced, 4 gathers per thread in flight
-    int32_t k = e0 + threadIdx.x;
-    for (; k + 3 * PR_THREADS < e1; k += 4 * PR_THREADS) {
-      const float g0 = gather_one<MODE>(a, k);
-      const float g1 = gather_one<MODE>(a, k + PR_THREADS);
-      const float g2 = gather_one<MODE>(a, k + 2 * PR_THREADS);
-      const float g3 = gather_one<MODE>(a, k + 3 * PR_THREADS);
-      stage[k - e0] = g0;
-      stage[k + PR_THREADS - e0] = g1;
-      stage[k + 2 * PR_THREADS - e0] = g2;
-      stage[k + 3 * PR_THREADS - e0] = g3;
-    }
-    for (; k < e1; k += PR_THREADS) stage[k - e0] = gather_one<MODE>(a, k);
-    __syncthreads();
-    // short rows: one thread each; longer rows: queued for the warps
-    for (int32_t i = r0 + threadIdx.x; i < r1; i += PR_THREADS) {
-      const int32_t b = a.rowptr[i], e = a.rowptr[i + 1];
-      if (e - b <= PR_SHORT) {
-        float acc = 0.0f;
-        for (int32_t q = b; q < e; q++) acc += stage[q - e0];
-        row_out<MODE>(a, i, acc, coef, resid, aux);
-      } else if (e - b <= PR_HEAVY) {
-        longrows[atomicAdd(&n_long, 1)] = i;
+  if (!hblk[wb]) {  // (a block that is one heavy row is summed by the chunk CTAs)
+    for (int32_t i = r0 + lane; i < r1; i += 32)  // empty rows
+      if (__ldg(rowptr + i) == __ldg(rowptr + i + 1)) row_out<MODE>(a, i, 0.0f, coef, resid, aux);
+    const int32_t e0 = __ldg(rowptr + r0), e1 = __ldg(rowptr + r1);
+    const int32_t kb = e0 & ~3;  // steps start 16-byte aligned
+    int32_t rc = r0;             // the row holding the first entry of the current step
+    float carry = 0.0f;          // the open part of the row running into the current step
+    int32_t cn[PR_EPL];
+    float vn[PR_EPL];
+    load_step<MODE>(a, kb + PR_EPL * lane, e0, e1, cn, vn);
+    for (int32_t gs = kb; gs < e1; gs += PR_STEP) {
+      const int32_t k0 = gs + PR_EPL * lane;
+      float g[PR_EPL];
+#pragma unroll
+      for (int j = 0; j < PR_EPL; j++) {
+        const float xv = cn[j] >= 0 ? __ldg(a.x + cn[j]) : 0.0f;
+        g[j] = MODE == 0 ? xv : vn[j] * xv;
       }
-    }
-    __syncthreads();
-    for (int q = warp; q < n_long; q += PR_THREADS / 32) {
-      const int32_t i = longrows[q];
-      const int32_t b = a.rowptr[i], e = a.rowptr[i + 1];
-      float acc = 0.0f;
-      for (int32_t k2 = b + lane; k2 < e; k2 += 32) acc += stage[k2 - e0];
-      acc = warp_sum(acc);
-      if (lane == 0) row_out<MODE>(a, i, acc, coef, resid, aux);
-    }
-  } else {
-    // the block holds a row longer than PR_HEAVY (gathered elsewhere), so its entries are not one
-    // short run: short rows one thread each straight from memory, longer rows one warp each
-    __syncthreads();  // n_long is initialised
-    for (int32_t i = r0 + threadIdx.x; i < r1; i += PR_THREADS) {
-      const int32_t b = a.rowptr[i], e = a.rowptr[i + 1];
-      if (e - b <= PR_SHORT) {
+      if (gs + PR_STEP < e1) load_step<MODE>(a, k0 + PR_STEP, e0, e1, cn, vn);
+      // this lane's entries [ks, ke)
+      const int32_t ks = max(k0, e0), ke = min(k0 + PR_EPL, e1);
+      float v = 0.0f;     // open part of the lane's last row (passed on by the scan)
+      bool fresh = false;  // the scan restarts at this lane (nothing open flows through it)
+      bool hclose = false;  // the lane closes a row that began before it (needs the joined prefix)
+      float hsum = 0.0f;
+      int32_t hrow = 0;
+      if (ks < ke) {
+        int32_t row = row_of(rowptr, rc, r1 - 1, ks);
+        int32_t rs = __ldg(rowptr + row), re = __ldg(rowptr + row + 1);
+        const bool open_head = rs < ks;
+        bool first = true;
         float acc = 0.0f;
-        for (int32_t q = b; q < e; q++) acc += gather_one<MODE>(a, q);
-        row_out<MODE>(a, i, acc, coef, resid, aux);
-      } else if (e - b <= PR_HEAVY) {
-        longrows[atomicAdd(&n_long, 1)] = i;
+#pragma unroll
+        for (int j = 0; j < PR_EPL; j++) {
+          const int32_t k = k0 + j;
+          if (k < ks || k >= ke) continue;
+          while (k >= re) {  // the row ended before k: close it, step over empty rows
+            if (re > rs) {
+              if (first && open_head) {
+                hclose = true;
+                hsum = acc;
+                hrow = row;
+              } else {
+                row_out<MODE>(a, row, acc, coef, resid, aux);
+              }
+            }
+            first = false;
+            acc = 0.0f;
+            row++;
+            rs = re;
+            re = __ldg(rowptr + row + 1);
+          }
+          acc += g[j];
+        }
+        if (re == ke) {  // the last row ends with this lane's entries
+          if (first && open_head) {
+            hclose = true;
+            hsum = acc;
+            hrow = row;
+          } else {
+            row_out<MODE>(a, row, acc, coef, resid, aux);
+          }
+          fresh = true;
+        } else {
+          v = acc;
+          fresh = !(first && open_head);
+        }
       }
-    }
-    __syncthreads();
-    for (int q = warp; q < n_long; q += PR_THREADS / 32) {
-      const int32_t i = longrows[q];
-      const int32_t b = a.rowptr[i], e = a.rowptr[i + 1];
-      float acc = 0.0f;
-      for (int32_t k2 = b + lane; k2 < e; k2 += 32) acc += gather_one<MODE>(a, k2);
-      acc = warp_sum(acc);
-      if (lane == 0) row_out<MODE>(a, i, acc, coef, resid, aux);
+      // segmented inclusive scan of (v, fresh) over the lanes; the step's carry enters at lane 0
+      float sv = v;
+      bool sf = fresh;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float tv = __shfl_up_sync(LAGR_FULL_MASK, sv, o);
+        const bool tf = __shfl_up_sync(LAGR_FULL_MASK, (int)sf, o) != 0;
+        if (lane >= o) {
+          if (!sf) sv += tv;
+          sf = sf || tf;
+        }
+      }
+      if (!sf) sv += carry;
+      float before = __shfl_up_sync(LAGR_FULL_MASK, sv, 1);
+      if (lane == 0) before = carry;
+      if (hclose) row_out<MODE>(a, hrow, before + hsum, coef, resid, aux);
+      carry = __shfl_sync(LAGR_FULL_MASK, sv, 31);
+      // the next step starts inside the row that holds this step's last entry
+      const int32_t klast = min(gs + PR_STEP, e1) - 1;
+      rc = row_of(rowptr, rc, r1 - 1, klast);
     }
   }
-  resid = block_sum(resid, red);
-  aux = block_sum(aux, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(resid, aux);
+  resid = warp_sum(resid);
+  aux = warp_sum(aux);
+  if (lane == 0) partials[wb] = make_double2(resid, aux);
 }
 
-// the rows longer than PR_HEAVY: add each row's chunk sums in chunk order, then the row's output
+// the rows longer than ROW_HEAVY: add each row's chunk sums in chunk order, then the row's output
 constexpr int PR_HF_THREADS = 256;
 template <int MODE>
 __global__ void __launch_bounds__(PR_HF_THREADS)
@@ -316,12 +395,18 @@ static inline int n_partials(const RowPlan &pl) {
   return np > PR_INIT_BLOCKS ? np : PR_INIT_BLOCKS;
 }
 
+static inline int aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 // one iteration: the row-block gather, the heavy rows, the fold of the partials
 template <int MODE>
 static void launch_iter(const RowPlan &pl, const IterArgs &a, PrState *st, double2 *partials, int32_t itermax,
                         double tol, cudaStream_t s) {
-  pr_stream<MODE><<<pl.nblk + pl.nhc, PR_THREADS, 0, s>>>(a, pl.blk, pl.nblk, pl.heavy, pl.hc_off, pl.hc_row, st,
-                                                           partials);
+  const int32_t nwb = (pl.nblk + PR_WARPS - 1) / PR_WARPS;
+  {
+    KTimer kt(TK_PR_GATHER, s);
+    pr_warp<MODE><<<nwb + pl.nhc, PR_THREADS, 0, s>>>(a, pl.blk, pl.nblk, pl.hblk, pl.heavy, pl.hc_off, pl.hc_row,
+                                                      st, partials);
+  }
   const int hfb = heavy_finish_blocks(pl);
   if (hfb > 0)
     pr_heavy_finish<MODE><<<hfb, PR_HF_THREADS, 0, s>>>(a, pl.heavy, pl.nheavy, pl.hc_off, st, partials + pl.nblk);
@@ -346,6 +431,7 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const in
                     const float *warm, float damping, float tol, int32_t itermax, int dangling, PrState *st,
                     int32_t *iters, double *resid, cudaStream_t s, char *msg) {
   const int32_t n = G->n;
+  const int vec = aligned16(colidx) && (val == nullptr || aligned16(val));
   Temp<float> buf1(s), w0(s), w1(s), hpart(s);
   Temp<double2> partials(s);
   LAGR_TRY(buf1.alloc(n, msg, "PageRank work vector"));
@@ -371,7 +457,7 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const in
     for (int c = 0; c < chunk; c++) {
       const int k = launched + c + 1;  // iteration number
       IterArgs a{rowptr, colidx, val, nullptr, x[(k - 1) & 1], x[k & 1], nullptr, sc, vvec, vuni, gvec, damping,
-                 dangling, hpart.p};
+                 dangling, hpart.p, vec};
       if (mode == 0) {
         a.x = w[(k - 1) & 1];
         a.wout = w[k & 1];
@@ -469,7 +555,7 @@ int pr_plan_enqueue(PrPlan *pl, float *out, const float *warm, int32_t iters, cu
   launch_init(0, pl->n, out, w[0], pl->sc, warm, pl->vvec, vuni, pl->st, pl->partials, pl->damping, 0, iters, 0.0, s);
   for (int k = 1; k <= iters; k++) {
     IterArgs a{pl->rowptr, pl->colidx, nullptr, w[(k - 1) & 1], x[(k - 1) & 1], x[k & 1], w[k & 1], pl->sc,
-               pl->vvec, vuni, nullptr, pl->damping, 0, pl->hpart};
+               pl->vvec, vuni, nullptr, pl->damping, 0, pl->hpart, aligned16(pl->colidx)};
     launch_iter<0>(pl->rows, a, pl->st, pl->partials, iters, 0.0, s);
   }
   LAGR_LAUNCH_CHECK();

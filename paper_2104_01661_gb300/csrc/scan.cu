@@ -1,5 +1,9 @@
 // Graph-store primitives: exclusive scan, stable radix sort, stable compaction of heavy rows and
 // the CSR -> CSC transpose (Property_AT, Sec. II-A).  All deterministic.
+#include <algorithm>
+#include <iterator>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace lagr {
@@ -370,20 +374,67 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
     set_msg(msg, "row plan: %s", cudaGetErrorString(e));
     st = LAGR_ERR_CUDA;
   }
-  const int64_t nblk = ((int64_t)light + n) / ROW_UNITS + 1;
+  // block starts: the first row at or after every ROW_UNITS-th unit, plus each heavy row and the
+  // row after it, so that every heavy row is a block of its own (merged on the host, once)
+  const int64_t nb0 = ((int64_t)light + n) / ROW_UNITS + 1;
   int32_t *blk = nullptr;
-  if (st == LAGR_OK) st = alloc_n(&blk, (size_t)nblk + 1, s, msg, "row blocks");
-  if (st == LAGR_OK) {
-    block_starts<<<grid_for(nblk + 1, 256), 256, 0, s>>>(lp.p, n, (int32_t)nblk, blk);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) {
+  uint8_t *hblk = nullptr;
+  int64_t nblk = 0;
+  {
+    Temp<int32_t> b0(s);
+    if (st == LAGR_OK) st = b0.alloc((size_t)nb0 + 1, msg, "row block starts");
+    if (st == LAGR_OK) {
+      block_starts<<<grid_for(nb0 + 1, 256), 256, 0, s>>>(lp.p, n, (int32_t)nb0, b0.p);
+      e = cudaGetLastError();
+    }
+    std::vector<int32_t> hb((size_t)nb0 + 1), hh((size_t)nheavy);
+    if (st == LAGR_OK && e == cudaSuccess)
+      e = cudaMemcpyAsync(hb.data(), b0.p, hb.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (st == LAGR_OK && e == cudaSuccess && nheavy > 0)
+      e = cudaMemcpyAsync(hh.data(), heavy, hh.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (st == LAGR_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st == LAGR_OK && e != cudaSuccess) {
       set_msg(msg, "row plan: %s", cudaGetErrorString(e));
       st = LAGR_ERR_CUDA;
+    }
+    if (st == LAGR_OK) {
+      std::vector<int32_t> hcut;  // heavy rows and the rows after them (ascending)
+      hcut.reserve(2 * hh.size());
+      for (int32_t h : hh) {
+        if (hcut.empty() || hcut.back() != h) hcut.push_back(h);
+        hcut.push_back(h + 1);
+      }
+      std::vector<int32_t> cut;  // every block start, then n
+      cut.reserve(hb.size() + hcut.size());
+      std::merge(hb.begin(), hb.end() - 1, hcut.begin(), hcut.end(), std::back_inserter(cut));
+      cut.erase(std::unique(cut.begin(), cut.end()), cut.end());
+      while (!cut.empty() && cut.back() >= n) cut.pop_back();
+      if (cut.empty() || cut.front() != 0) cut.insert(cut.begin(), 0);
+      nblk = (int64_t)cut.size();
+      cut.push_back(n);
+      std::vector<uint8_t> flag((size_t)nblk, 0);
+      size_t q = 0;
+      for (int64_t b = 0; b < nblk && q < hh.size(); b++) {
+        while (q < hh.size() && hh[q] < cut[b]) q++;
+        if (q < hh.size() && hh[q] == cut[b] && cut[b + 1] == cut[b] + 1) flag[b] = 1;
+      }
+      st = alloc_n(&blk, (size_t)nblk + 1, s, msg, "row blocks");
+      if (st == LAGR_OK) st = alloc_n(&hblk, (size_t)nblk, s, msg, "heavy block flags");
+      if (st == LAGR_OK) e = cudaMemcpyAsync(blk, cut.data(), cut.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+      if (st == LAGR_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(hblk, flag.data(), flag.size(), cudaMemcpyHostToDevice, s);
+      // the host vectors must outlive the copies
+      if (st == LAGR_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (st == LAGR_OK && e != cudaSuccess) {
+        set_msg(msg, "row plan: %s", cudaGetErrorString(e));
+        st = LAGR_ERR_CUDA;
+      }
     }
   }
   if (st < 0) {
     dev_free(heavy, s);
     dev_free(blk, s);
+    dev_free(hblk, s);
     return st;
   }
   // chunks of the heavy rows
@@ -419,6 +470,7 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
     dev_free(blk, s);
     dev_free(hc_off, s);
     dev_free(hc_row, s);
+    dev_free(hblk, s);
     return st;
   }
   pl->heavy = heavy;
@@ -428,6 +480,7 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
   pl->hc_off = hc_off;
   pl->hc_row = hc_row;
   pl->nhc = nhc;
+  pl->hblk = hblk;
   return LAGR_OK;
 }
 

@@ -1,20 +1,22 @@
 // Triangle counting (Alg. 6, Sec. IV-F): t = sum(C) with C<s(L)> = L plus.pair U', fused so
 // that C is never formed (the materialised C is what the paper blames for its 3x gap to GAP).
 //
-// Orientation.  Alg. 6 relabels A by ascending degree (A(p,p)) and splits it into L = tril and
-// U = triu.  Relabelling by the stable ascending-degree permutation is the same as ordering the
-// vertices by the pair (degree, id); this file keeps the original labels and builds
-//   U(v,:) = { u in A(v,:) : key(u) > key(v) },  key = (deg, id) when sorting, id otherwise,
-// which is triu(A(p,p),1) up to the renaming.  L = U' so, for every stored (i,j) of L,
-// C(i,j) = |L(i,:) n U(j,:)| = |U(j,:) n U(i,:)|: the count of every undirected edge {x,y} is
-// the intersection of the two oriented lists.  Summed over edges this counts each triangle
-// exactly once (only its two lowest vertices' edge sees the third).
+// Labels.  Alg. 6 relabels A by the ascending-degree permutation p (A(p,p)) before splitting it
+// into L = tril and U = triu.  Here p comes from a stable radix sort of the degrees (ties by id),
+// and rank[v] is v's position in it (rank[v] = v when Alg. 6 decides not to sort).  The rows of A
+// are not moved: U(v,:) = { rank(u) : u in A(v,:), rank(u) > rank(v) } is stored for every
+// original vertex v, its entries being ranks, which is triu(A(p,p),1) with the rows renamed back.
+// L = U', so for every stored (i,j) of L, C(i,j) = |L(i,:) n U(j,:)| = |U(i,:) n U(j,:)| in rank
+// space: the count of each undirected edge {x,y} is the intersection of the two oriented lists,
+// and summed over the edges this counts each triangle once.
 //
 // Intersection.  Each edge {x,y} is anchored at the endpoint with the larger (d+, id); the
-// anchor's list U(x,:) goes into a shared-memory hash table once and the other endpoint's
-// (shorter) list is streamed and probed.  Anchors with short lists run one per warp; anchors
-// with long lists or many neighbours run one CTA per (anchor, chunk of neighbours).  Inside a
-// warp, the 32 lists of a batch of neighbours are walked load-balanced (warp_segments).
+// anchor's list goes into a shared-memory set once and the other (shorter) list is probed.  The
+// set is a bitmap over the top ranks (the window) plus a small hash table for the entries below
+// it: after the degree ordering nearly every entry of a long list is a high-degree vertex, so a
+// probe is one shared-memory word, and an entry ranked below the anchor is rejected without any
+// lookup (it cannot be in the anchor's list).  Anchors with short lists run one per warp; long
+// lists or many neighbours run one CTA per (anchor, chunk of neighbours).
 #include <cstring>
 
 #include "internal.cuh"
@@ -23,28 +25,30 @@ namespace lagr {
 namespace {
 
 constexpr int TCW_WARPS = 8;          // warps per CTA in the warp-anchor kernel
-constexpr int TCW_SLOTS = 512;        // hash slots per warp
+constexpr int TCW_SLOTS = 512;        // hash slots per warp (entries below the window)
 constexpr int TCW_MAXD = TCW_SLOTS / 2;  // warp anchors: d+ <= wmax <= 256 ...
 constexpr int TCW_MAXDEG = 4096;      // ... and degree <= 4096
+constexpr int TCW_CHUNK = 256;       // warp anchors with more neighbours are cut into items of this many
+constexpr int TCW_GRAB = 8;          // short warp anchors taken per queue atomic
+constexpr int TCW_WIN_LOG = 15;       // per-warp window: the top 32768 ranks (4 KB of bits)
 constexpr int TCC_THREADS = 512;      // CTA-anchor kernel
-constexpr int TCC_SLOTS = 8192;       // hash slots per CTA (32 KB); d+ > 4096 uses binary search
-constexpr int TCW_FILTER_BITS_LOG = 11;  // bit filter per warp: 2048 bits
-constexpr int TCC_FILTER_BITS_LOG = 15;  // bit filter per CTA: 32768 bits (4 KB)
+constexpr int TCC_SLOTS = 8192;       // hash slots per CTA (32 KB)
+constexpr int TCC_WIN_LOG = 17;       // per-CTA window: the top 131072 ranks (16 KB of bits)
 constexpr int TCC_CHUNK = 2048;       // default neighbours per CTA work item
 constexpr int32_t EMPTY = -1;
+constexpr size_t TCW_SMEM = (size_t)TCW_WARPS * (((1 << TCW_WIN_LOG) / 32) * 4 + TCW_SLOTS * 4);
+constexpr size_t TCC_SMEM = ((1 << TCC_WIN_LOG) / 32) * 4 + TCC_SLOTS * 4;
 
 // slots of the per-graph device scalars used here
 constexpr int SL_SORT = SC_COUNT0;
 constexpr int SL_DECIDE = SC_COUNT1;
 constexpr int SL_NW = SC_COUNT2;
 constexpr int SL_NC = SC_COUNT3;
-constexpr int SL_QW = SC_COUNT5;
+constexpr int SL_NWL = SC_COUNT4;  // warp anchors with at most TCW_CHUNK neighbours (one item each)
+constexpr int SL_QW = SC_COUNT5;   // queue cursor of the chunked warp items (SL_NW of them)
 constexpr int SL_QC = SC_COUNT6;
 constexpr int SL_TOTAL = SC_COUNT7;
-
-__device__ __forceinline__ bool keep_edge(int32_t u, int32_t v, int32_t du, int32_t dv, int sort) {
-  return sort ? (du > dv || (du == dv && u > v)) : (u > v);
-}
+constexpr int SL_QWL = SC_COUNT8;  // queue cursor of the short warp anchors
 
 __device__ __forceinline__ uint32_t hslot(int32_t w, int logT) {
   return ((uint32_t)w * 0x9E3779B1u) >> (32 - logT);
@@ -53,48 +57,53 @@ __device__ __forceinline__ uint32_t hslot(int32_t w, int logT) {
 __device__ __forceinline__ void hinsert(int32_t *tab, int logT, int32_t w) {
   const uint32_t mask = (1u << logT) - 1;
   uint32_t h = hslot(w, logT);
-  while (atomicCAS(&tab[h], EMPTY, w) != EMPTY) h = (h + 1) & mask;
+  // the table holds at least twice the entries inserted, so a free slot exists; the bound only
+  // guarantees termination
+  for (uint32_t i = 0; i <= mask && atomicCAS(&tab[h], EMPTY, w) != EMPTY; i++) h = (h + 1) & mask;
 }
 
 __device__ __forceinline__ int hprobe(const int32_t *tab, int logT, int32_t w) {
   const uint32_t mask = (1u << logT) - 1;
   uint32_t h = hslot(w, logT);
-  for (;;) {
+  for (uint32_t i = 0; i <= mask; i++) {
     const int32_t v = tab[h];
     if (v == w) return 1;
     if (v == EMPTY) return 0;
     h = (h + 1) & mask;
   }
+  return 0;
 }
 
-// A set of U(x,:) in shared memory: a bit filter (one bit per hashed value, logM bits wide) in
-// front of an open-addressing table.  Most probes miss (a wedge closes a triangle less than one
-// time in five on the R-MAT graphs), and a miss usually costs one filter word.
-struct HashSet {
+// The anchor's list as a set of ranks: a bitmap over the window [w0, w0 + window) and a hash table
+// for the entries below w0.  `scan` (CTA anchors only): too many entries below the window for the
+// table, so those are found by scanning the list in memory instead.
+struct RankSet {
+  uint32_t *bm;
   int32_t *tab;
-  uint32_t *bits;
-  int logT, logM;
-  __device__ __forceinline__ uint32_t fslot(int32_t w) const { return ((uint32_t)w * 0x85EBCA77u) >> (32 - logM); }
+  int logT;
+  int32_t w0, rx;
+  const int32_t *list;  // the anchor's list in memory (scan mode)
+  int32_t len;
+  bool scan;   // entries below the window are found by scanning `list`
+  bool below;  // the anchor has entries below the window (otherwise the table is not used at all)
   __device__ __forceinline__ void insert(int32_t w) const {
-    const uint32_t f = fslot(w);
-    atomicOr(&bits[f >> 5], 1u << (f & 31));
-    hinsert(tab, logT, w);
+    if (w >= w0) atomicOr(&bm[(w - w0) >> 5], 1u << ((w - w0) & 31));
+    else if (!scan) hinsert(tab, logT, w);
   }
-  __device__ __forceinline__ int has(int32_t w) const {
-    const uint32_t f = fslot(w);
-    if (!((bits[f >> 5] >> (f & 31)) & 1u)) return 0;
-    return hprobe(tab, logT, w);
+  __device__ __forceinline__ void erase(int32_t w) const {
+    if (w >= w0) bm[(w - w0) >> 5] = 0u;
+  }
+  __device__ __forceinline__ uint32_t has(int32_t w) const {
+    const int32_t d = w - w0;
+    // in the window the bitmap decides alone (it holds no rank <= rx)
+    if (d >= 0) return (bm[d >> 5] >> (d & 31)) & 1u;
+    if (w <= rx || !below) return 0;  // the anchor's entries all rank above it
+    if (!scan) return (uint32_t)hprobe(tab, logT, w);
+    for (int32_t q = 0; q < len; q++)
+      if (list[q] == w) return 1;
+    return 0;
   }
 };
-
-__device__ __forceinline__ int bsearch_has(const int32_t *__restrict__ a, int32_t len, int32_t w) {
-  int32_t lo = 0, hi = len;
-  while (lo < hi) {
-    const int32_t mid = (lo + hi) >> 1;
-    if (a[mid] < w) lo = mid + 1; else hi = mid;
-  }
-  return lo < len && a[lo] == w;
-}
 
 __device__ __forceinline__ int ceil_log2(int32_t x) {  // x >= 1
   return x <= 1 ? 0 : 32 - __clz(x - 1);
@@ -129,26 +138,44 @@ __global__ void tc_set_mode(int32_t n, int method, int64_t *__restrict__ dscal) 
   dscal[SL_SORT] = sort;
 }
 
+// keys = degrees, vals = ids: their stable sort is the ascending-degree permutation of Alg. 6
+__global__ void tc_rank_keys(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ keys,
+                             int32_t *__restrict__ vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    keys[i] = rowptr[i + 1] - rowptr[i];
+    vals[i] = (int32_t)i;
+  }
+}
+
+// rank[p[i]] = i after sorting, rank[v] = v when Alg. 6 does not sort
+__global__ void tc_rank_scatter(const int32_t *__restrict__ vals, int32_t n, const int64_t *__restrict__ dscal,
+                                int32_t *__restrict__ rank) {
+  const int sort = (int)dscal[SL_SORT];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (sort) rank[vals[i]] = (int32_t)i;
+    else rank[i] = (int32_t)i;
+  }
+}
+
 // ---- orientation: d+ per vertex, then the oriented rows -------------------------------------------
 
-// One CTA per row block (see RowPlan): the degrees of the block's neighbours are gathered into
+// One CTA per row block (see RowPlan): the ranks of the block's neighbours are gathered into
 // shared memory with coalesced colidx loads, then each short row is oriented by one thread and
-// each longer row by one warp.  FILL = false counts d+(v); FILL = true writes U(v,:) in the order
-// of A(v,:) (ballots keep the order inside a warp).  Rows longer than ROW_HEAVY are left to the
-// heavy kernels.
+// each longer row by one warp.  FILL = false counts d+(v); FILL = true writes U(v,:) (the ranks
+// above rank(v), in the order of A(v,:); ballots keep the order inside a warp).  Rows longer than
+// ROW_HEAVY are left to the heavy kernels.
 constexpr int OR_STAGE = ROW_UNITS + ROW_HEAVY + 64;
 constexpr int OR_SHORT = 32;
 
 template <bool FILL>
 __global__ void __launch_bounds__(256)
     tc_orient_rows(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                   const int32_t *__restrict__ deg, const int32_t *__restrict__ blk, int64_t *__restrict__ dscal,
+                   const int32_t *__restrict__ rank, const int32_t *__restrict__ blk, int64_t *__restrict__ dscal,
                    int32_t *__restrict__ dplus, const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx,
                    int64_t ucap) {
   __shared__ int32_t stage[OR_STAGE];
   __shared__ int32_t longrows[ROW_UNITS / (OR_SHORT + 1) + 2];
   __shared__ int n_long;
-  const int sort = (int)dscal[SL_SORT];
   const int32_t r0 = blk[blockIdx.x], r1 = blk[blockIdx.x + 1];
   const int32_t e0 = rowptr[r0], e1 = rowptr[r1];
   const bool staged = e1 - e0 <= OR_STAGE;
@@ -157,38 +184,36 @@ __global__ void __launch_bounds__(256)
   if (staged) {
     int32_t k = e0 + threadIdx.x;
     for (; k + 3 * 256 < e1; k += 4 * 256) {
-      const int32_t d0 = __ldg(&deg[colidx[k]]);
-      const int32_t d1 = __ldg(&deg[colidx[k + 256]]);
-      const int32_t d2 = __ldg(&deg[colidx[k + 512]]);
-      const int32_t d3 = __ldg(&deg[colidx[k + 768]]);
+      const int32_t d0 = __ldg(&rank[colidx[k]]);
+      const int32_t d1 = __ldg(&rank[colidx[k + 256]]);
+      const int32_t d2 = __ldg(&rank[colidx[k + 512]]);
+      const int32_t d3 = __ldg(&rank[colidx[k + 768]]);
       stage[k - e0] = d0;
       stage[k + 256 - e0] = d1;
       stage[k + 512 - e0] = d2;
       stage[k + 768 - e0] = d3;
     }
-    for (; k < e1; k += 256) stage[k - e0] = __ldg(&deg[colidx[k]]);
+    for (; k < e1; k += 256) stage[k - e0] = __ldg(&rank[colidx[k]]);
   }
   __syncthreads();
-  auto du_of = [&](int32_t q, int32_t u) { return staged ? stage[q - e0] : __ldg(&deg[u]); };
+  auto ru_of = [&](int32_t q) { return staged ? stage[q - e0] : __ldg(&rank[colidx[q]]); };
   for (int32_t v = r0 + threadIdx.x; v < r1; v += 256) {
     const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
     if (dv <= OR_SHORT) {
+      const int32_t rv = rank[v];
       if (FILL) {
         int64_t out = u_rowptr[v];
         for (int32_t q = b; q < e; q++) {
-          const int32_t u = colidx[q];
-          if (keep_edge(u, v, du_of(q, u), dv, sort)) {
-            if (out < ucap) u_colidx[out] = u;
+          const int32_t ru = ru_of(q);
+          if (ru > rv) {
+            if (out < ucap) u_colidx[out] = ru;
             else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
             out++;
           }
         }
       } else {
         int cnt = 0;
-        for (int32_t q = b; q < e; q++) {
-          const int32_t u = colidx[q];
-          cnt += keep_edge(u, v, du_of(q, u), dv, sort);
-        }
+        for (int32_t q = b; q < e; q++) cnt += ru_of(q) > rv;
         dplus[v] = cnt;
       }
     } else if (dv <= ROW_HEAVY) {
@@ -199,22 +224,22 @@ __global__ void __launch_bounds__(256)
   const unsigned lt = lanemask_lt();
   for (int q = warp; q < n_long; q += 8) {
     const int32_t v = longrows[q];
-    const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
+    const int32_t b = rowptr[v], e = rowptr[v + 1], rv = rank[v];
     int64_t out = FILL ? u_rowptr[v] : 0;
     int cnt = 0;
     for (int32_t base = b; base < e; base += 32) {
       const int32_t k = base + lane;
-      int32_t u = 0;
+      int32_t ru = 0;
       bool f = false;
       if (k < e) {
-        u = colidx[k];
-        f = keep_edge(u, v, du_of(k, u), dv, sort);
+        ru = ru_of(k);
+        f = ru > rv;
       }
       if (FILL) {
         const unsigned bal = __ballot_sync(LAGR_FULL_MASK, f);
         if (f) {
           const int64_t pos = out + __popc(bal & lt);
-          if (pos < ucap) u_colidx[pos] = u;
+          if (pos < ucap) u_colidx[pos] = ru;
           else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
         }
         out += __popc(bal);
@@ -230,42 +255,37 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void tc_orient_count_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                      const int32_t *__restrict__ deg, int64_t *__restrict__ dscal,
-                                      int32_t *__restrict__ dplus, const int32_t *__restrict__ heavy, int32_t nh) {
+                                      const int32_t *__restrict__ rank, int32_t *__restrict__ dplus,
+                                      const int32_t *__restrict__ heavy, int32_t nh) {
   __shared__ int red[32];
-  const int sort = (int)dscal[SL_SORT];
   for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
     const int32_t v = heavy[h];
-    const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
+    const int32_t b = rowptr[v], e = rowptr[v + 1], rv = rank[v];
     int cnt = 0;
-    for (int32_t k = b + threadIdx.x; k < e; k += blockDim.x) {
-      const int32_t u = colidx[k];
-      cnt += keep_edge(u, v, deg[u], dv, sort);
-    }
+    for (int32_t k = b + threadIdx.x; k < e; k += blockDim.x) cnt += __ldg(&rank[colidx[k]]) > rv;
     cnt = block_sum(cnt, red);
     if (threadIdx.x == 0) dplus[v] = cnt;
   }
 }
 
 __global__ void tc_orient_fill_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                     const int32_t *__restrict__ deg, int64_t *__restrict__ dscal,
+                                     const int32_t *__restrict__ rank, int64_t *__restrict__ dscal,
                                      const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx,
                                      int64_t ucap, const int32_t *__restrict__ heavy, int32_t nh) {
   __shared__ int wc[32];
-  const int sort = (int)dscal[SL_SORT];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const unsigned lt = lanemask_lt();
   for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
     const int32_t v = heavy[h];
-    const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
+    const int32_t b = rowptr[v], e = rowptr[v + 1], rv = rank[v];
     int64_t out = u_rowptr[v];
     for (int32_t base = b; base < e; base += blockDim.x) {
       const int32_t k = base + threadIdx.x;
       int32_t u = 0;
       bool f = false;
       if (k < e) {
-        u = colidx[k];
-        f = keep_edge(u, v, deg[u], dv, sort);
+        u = __ldg(&rank[colidx[k]]);
+        f = u > rv;
       }
       const unsigned bal = __ballot_sync(LAGR_FULL_MASK, f);
       if (lane == 0) wc[warp] = __popc(bal);
@@ -289,8 +309,9 @@ __global__ void tc_orient_fill_heavy(const int32_t *__restrict__ rowptr, const i
 // ---- anchors: warp class (short list, moderate degree) and CTA items -------------------------------
 
 __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus, int32_t n,
-                            int32_t *__restrict__ listw, int2 *__restrict__ listc, int64_t capc,
-                            int64_t *__restrict__ dscal, int wmax, int chunk) {
+                            int32_t *__restrict__ listw, int2 *__restrict__ listwh, int64_t capwh,
+                            int2 *__restrict__ listc, int64_t capc, int64_t *__restrict__ dscal, int wmax,
+                            int chunk) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -304,12 +325,25 @@ __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *_
     const bool active = a > 0;
     const bool is_w = active && a <= wmax && dg <= TCW_MAXDEG;
     const int nch = (active && !is_w) ? (dg + chunk - 1) / chunk : 0;
-    // warp-class anchors
-    const unsigned bw = __ballot_sync(LAGR_FULL_MASK, is_w);
+    // warp-class anchors: one item each when they have at most TCW_CHUNK neighbours, else one
+    // item per TCW_CHUNK neighbours (so that no warp item is much longer than the others)
+    const bool wl = is_w && dg <= TCW_CHUNK;
+    const unsigned bl = __ballot_sync(LAGR_FULL_MASK, wl);
+    unsigned long long pl = 0;
+    if (lane == 0 && bl) pl = atomicAdd((unsigned long long *)&dscal[SL_NWL], (unsigned long long)__popc(bl));
+    pl = __shfl_sync(LAGR_FULL_MASK, pl, 0);
+    if (wl) listw[pl + __popc(bl & lt)] = (int32_t)v;
+    const int nwi = (is_w && !wl) ? (dg + TCW_CHUNK - 1) / TCW_CHUNK : 0;
+    const int winc = warp_inclusive_scan(nwi);
+    const int wtot = __shfl_sync(LAGR_FULL_MASK, winc, 31);
     unsigned long long pw = 0;
-    if (lane == 0 && bw) pw = atomicAdd((unsigned long long *)&dscal[SL_NW], (unsigned long long)__popc(bw));
-    pw = __shfl_sync(LAGR_FULL_MASK, pw, 0);
-    if (is_w) listw[pw + __popc(bw & lt)] = (int32_t)v;
+    if (lane == 31 && wtot) pw = atomicAdd((unsigned long long *)&dscal[SL_NW], (unsigned long long)wtot);
+    pw = __shfl_sync(LAGR_FULL_MASK, pw, 31);
+    for (int c = 0; c < nwi; c++) {
+      const int64_t p = (int64_t)pw + winc - nwi + c;
+      if (p < capwh) listwh[p] = make_int2((int32_t)v, c * TCW_CHUNK);
+      else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
+    }
     // CTA items, one per chunk of `chunk` neighbours
     const int incl = warp_inclusive_scan(nch);
     const int tot = __shfl_sync(LAGR_FULL_MASK, incl, 31);
@@ -335,7 +369,7 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
                                                            const int32_t *__restrict__ u_colidx,
                                                            const int32_t *__restrict__ dplus, Probe &&probe) {
   const int lane = threadIdx.x & 31;
-  unsigned long long c = 0;
+  uint32_t c = 0;  // this lane's matches in the batch: fewer than nnz, so 32 bits hold them
   const int32_t j = jb + lane;
   int32_t st = 0, len = 0;
   if (j < e) {
@@ -354,7 +388,13 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
   const unsigned total = __reduce_add_sync(LAGR_FULL_MASK, (unsigned)slen);
   const unsigned lmax = __reduce_max_sync(LAGR_FULL_MASK, (unsigned)slen);
   if (32u * lmax <= 2u * total) {
-    for (int32_t q = 0; q < slen; q++) c += probe(u_colidx[st + q]);
+    const int32_t *lst = u_colidx + st;
+    int32_t q = 0;
+    for (; q + 3 < slen; q += 4) {  // four independent loads in flight
+      const int32_t w0 = lst[q], w1 = lst[q + 1], w2 = lst[q + 2], w3 = lst[q + 3];
+      c += probe(w0) + probe(w1) + probe(w2) + probe(w3);
+    }
+    for (; q < slen; q++) c += probe(lst[q]);
   } else if (total > 0) {
     warp_segments(st, slen, 0, [&](bool valid, int, int, int gidx) {
       if (valid) c += probe(u_colidx[gidx]);
@@ -375,38 +415,39 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
   return c;
 }
 
-__global__ void __launch_bounds__(TCW_WARPS * 32, 6)
+__global__ void __launch_bounds__(TCW_WARPS * 32, 4)
     tc_count_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                   const int32_t *__restrict__ u_rowptr, const int32_t *__restrict__ u_colidx,
-                  const int32_t *__restrict__ dplus, const int32_t *__restrict__ listw, int64_t *__restrict__ dscal,
+                  const int32_t *__restrict__ dplus, const int32_t *__restrict__ rank,
+                  const int32_t *__restrict__ listw, const int2 *__restrict__ listwh, int64_t capwh,
+                  int64_t *__restrict__ dscal, int32_t w0,
                   const int32_t *__restrict__ voff, int32_t ngraphs, unsigned long long *__restrict__ counts) {
-  __shared__ int32_t tab_all[TCW_WARPS][TCW_SLOTS];
-  __shared__ uint32_t bits_all[TCW_WARPS][(1 << TCW_FILTER_BITS_LOG) / 32];
+  extern __shared__ uint32_t wsm[];  // per warp: window bits, then hash slots
   __shared__ unsigned long long red[32];
+  constexpr int WORDS = (1 << TCW_WIN_LOG) / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t *tab = tab_all[warp];
-  uint32_t *bits = bits_all[warp];
-  const int64_t nw = dscal[SL_NW];
+  uint32_t *bm = wsm + warp * (WORDS + TCW_SLOTS);
+  int32_t *tab = reinterpret_cast<int32_t *>(bm + WORDS);
+  for (int i = lane; i < WORDS; i += 32) bm[i] = 0u;
+  __syncwarp();
+  const int64_t nwh = min(dscal[SL_NW], capwh), nwl = dscal[SL_NWL];
   unsigned long long mine = 0;
-  for (;;) {
-    long long it = 0;
-    if (lane == 0) it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QW], 1ull);
-    it = __shfl_sync(LAGR_FULL_MASK, it, 0);
-    if (it >= nw) break;
-    const int32_t x = listw[it];
+  // one warp item: the anchor x's neighbours [jb0, je) against x's set
+  auto item = [&](int32_t x, int32_t jb0, int32_t je) {
     const int32_t a = dplus[x];
-    const HashSet hs{tab, bits, ceil_log2(2 * a), TCW_FILTER_BITS_LOG};
-    const int T = 1 << hs.logT;
-    for (int i = lane; i < T; i += 32) tab[i] = EMPTY;
-    for (int i = lane; i < (1 << TCW_FILTER_BITS_LOG) / 32; i += 32) bits[i] = 0u;
-    __syncwarp();
     const int32_t ub = u_rowptr[x];
-    for (int i = lane; i < a; i += 32) hs.insert(u_colidx[ub + i]);
+    // the table is cleared for every item, so it is valid whether or not entries fall below w0
+    const RankSet rs{bm, tab, ceil_log2(2 * a), w0, rank[x], nullptr, 0, false, true};
+    const int T = 1 << rs.logT;
+    for (int i = lane; i < T; i += 32) tab[i] = EMPTY;
+    __syncwarp();
+    for (int i = lane; i < a; i += 32) rs.insert(u_colidx[ub + i]);
     __syncwarp();
     unsigned long long c = 0;
-    const int32_t e = rowptr[x + 1];
-    for (int32_t jb = rowptr[x]; jb < e; jb += 32)
-      c += anchor_batch(x, a, jb, e, colidx, u_rowptr, u_colidx, dplus, [&](int32_t w) { return hs.has(w); });
+    for (int32_t jb = jb0; jb < je; jb += 32)
+      c += anchor_batch(x, a, jb, je, colidx, u_rowptr, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
+    __syncwarp();
+    for (int i = lane; i < a; i += 32) rs.erase(u_colidx[ub + i]);
     if (voff) {
       c = warp_sum(c);
       if (lane == 0 && c) atomicAdd(&counts[member_of(voff, ngraphs, x)], c);
@@ -414,6 +455,29 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 6)
       mine += c;
     }
     __syncwarp();
+  };
+  // first the chunked items of the long anchors, one per queue atomic
+  for (;;) {
+    long long it = 0;
+    if (lane == 0) it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QW], 1ull);
+    it = __shfl_sync(LAGR_FULL_MASK, it, 0);
+    if (it >= nwh) break;
+    const int2 w = listwh[it];
+    const int32_t jb0 = rowptr[w.x] + w.y;
+    item(w.x, jb0, min(rowptr[w.x + 1], jb0 + TCW_CHUNK));
+  }
+  // then the short anchors, TCW_GRAB per queue atomic (most of them are tiny: one atomic each
+  // would serialise the warps on the counter)
+  for (;;) {
+    long long it = 0;
+    if (lane == 0) it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QWL], (unsigned long long)TCW_GRAB);
+    it = __shfl_sync(LAGR_FULL_MASK, it, 0);
+    if (it >= nwl) break;
+    const long long it_end = min(it + TCW_GRAB, (long long)nwl);
+    for (; it < it_end; it++) {
+      const int32_t x = listw[it];
+      item(x, rowptr[x], rowptr[x + 1]);
+    }
   }
   if (!voff) {
     mine = block_sum(mine, red);
@@ -424,21 +488,26 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 6)
 __global__ void __launch_bounds__(TCC_THREADS)
     tc_count_cta(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                  const int32_t *__restrict__ u_rowptr, const int32_t *__restrict__ u_colidx,
-                 const int32_t *__restrict__ dplus, const int2 *__restrict__ listc, int64_t *__restrict__ dscal,
-                 const int32_t *__restrict__ voff, int32_t ngraphs, unsigned long long *__restrict__ counts,
-                 int chunk, int64_t capc) {
-  extern __shared__ int32_t tab[];  // TCC_SLOTS hash slots, then the bit filter
-  uint32_t *bits = reinterpret_cast<uint32_t *>(tab + TCC_SLOTS);
+                 const int32_t *__restrict__ dplus, const int32_t *__restrict__ rank, const int2 *__restrict__ listc,
+                 int64_t *__restrict__ dscal, int32_t w0, const int32_t *__restrict__ voff, int32_t ngraphs,
+                 unsigned long long *__restrict__ counts, int chunk, int64_t capc) {
+  extern __shared__ uint32_t csm[];  // window bits, then hash slots
+  constexpr int WORDS = (1 << TCC_WIN_LOG) / 32;
+  uint32_t *bm = csm;
+  int32_t *tab = reinterpret_cast<int32_t *>(csm + WORDS);
   __shared__ long long s_it;
   __shared__ int32_t s_next;  // next neighbour batch of the current item
+  __shared__ int32_t s_below;  // entries of the anchor's list below the window
   __shared__ unsigned long long red[32];
   const int lane = threadIdx.x & 31;
   const int64_t nc = min(dscal[SL_NC], capc);  // never read past the list (an overflow sets SC_ERR)
+  for (int i = threadIdx.x; i < WORDS; i += blockDim.x) bm[i] = 0u;
   unsigned long long mine = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       s_it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QC], 1ull);
       if (s_it < nc) s_next = rowptr[listc[s_it].x] + listc[s_it].y;
+      s_below = 0;
     }
     __syncthreads();
     const long long it = s_it;
@@ -447,16 +516,22 @@ __global__ void __launch_bounds__(TCC_THREADS)
     const int32_t x = item.x;
     const int32_t a = dplus[x];
     const int32_t ub = u_rowptr[x];
-    const bool hashed = a <= TCC_SLOTS / 2;
-    const HashSet hs{tab, bits, hashed ? ceil_log2(2 * a) : 1, TCC_FILTER_BITS_LOG};
-    if (hashed) {
-      const int T = 1 << hs.logT;
+    // how many entries fall below the window decides between the hash table and a scan
+    int below = 0;
+    for (int i = threadIdx.x; i < a; i += blockDim.x) below += u_colidx[ub + i] < w0;
+    below = __reduce_add_sync(LAGR_FULL_MASK, below);
+    if (lane == 0 && below) atomicAdd(&s_below, below);
+    __syncthreads();
+    const int32_t nb = s_below;
+    const bool scan = nb > TCC_SLOTS / 2;
+    const RankSet rs{bm, tab, (nb > 0 && !scan) ? ceil_log2(2 * nb) : 1, w0, rank[x], u_colidx + ub, a, scan, nb > 0};
+    if (nb > 0 && !scan) {
+      const int T = 1 << rs.logT;
       for (int i = threadIdx.x; i < T; i += blockDim.x) tab[i] = EMPTY;
-      for (int i = threadIdx.x; i < (1 << TCC_FILTER_BITS_LOG) / 32; i += blockDim.x) bits[i] = 0u;
-      __syncthreads();
-      for (int i = threadIdx.x; i < a; i += blockDim.x) hs.insert(u_colidx[ub + i]);
       __syncthreads();
     }
+    for (int i = threadIdx.x; i < a; i += blockDim.x) rs.insert(u_colidx[ub + i]);
+    __syncthreads();
     const int32_t b = rowptr[x] + item.y;
     const int32_t e = min(rowptr[x + 1], b + chunk);
     unsigned long long c = 0;
@@ -466,11 +541,7 @@ __global__ void __launch_bounds__(TCC_THREADS)
       if (lane == 0) jb = atomicAdd(&s_next, 32);
       jb = __shfl_sync(LAGR_FULL_MASK, jb, 0);
       if (jb >= e) break;
-      if (hashed)
-        c += anchor_batch(x, a, jb, e, colidx, u_rowptr, u_colidx, dplus, [&](int32_t w) { return hs.has(w); });
-      else
-        c += anchor_batch(x, a, jb, e, colidx, u_rowptr, u_colidx, dplus,
-                          [&](int32_t w) { return bsearch_has(u_colidx + ub, a, w); });
+      c += anchor_batch(x, a, jb, e, colidx, u_rowptr, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
     }
     if (voff) {
       c = warp_sum(c);
@@ -478,6 +549,8 @@ __global__ void __launch_bounds__(TCC_THREADS)
     } else {
       mine += c;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < a; i += blockDim.x) rs.erase(u_colidx[ub + i]);
     __syncthreads();
   }
   if (!voff) {
@@ -513,12 +586,20 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
   G->u_rowptr = G->u_colidx = nullptr;
   dev_free(P->tc_dplus, s);
   dev_free(P->tc_listw, s);
+  dev_free(P->tc_listwh, s);
   dev_free(P->tc_listc, s);
   dev_free(P->tc_scan, s);
+  dev_free(P->tc_rank, s);
+  dev_free(P->tc_sortbuf, s);
+  dev_free(P->tc_radix, s);
+  dev_free(P->tc_radix_scan, s);
   P->tc_scan = nullptr;
-  P->tc_dplus = P->tc_listw = nullptr;
+  P->tc_radix_scan = nullptr;
+  P->tc_dplus = P->tc_listw = P->tc_rank = P->tc_sortbuf = P->tc_radix = nullptr;
   P->tc_listc = nullptr;
+  P->tc_listwh = nullptr;
   P->tc_capc = 0;
+  P->tc_capwh = 0;
   G->u_order = -1;
   LAGR_TRY(lagr_property_row_degree(G, s, msg));
   LAGR_TRY(lagr_property_AT(G, s, msg));  // undirected: A' aliases A, so the row plan is shared
@@ -527,8 +608,16 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
   LAGR_TRY(alloc_n(&G->u_rowptr, (size_t)n + 1, s, msg, "U row pointers"));
   LAGR_TRY(alloc_n(&G->u_colidx, (size_t)(nnz / 2 + 1), s, msg, "U column indices"));
   LAGR_TRY(alloc_n(&P->tc_listw, (size_t)n + 1, s, msg, "warp anchors"));
+  // warp anchors cut into items: ceil(deg / TCW_CHUNK) <= 2 deg / TCW_CHUNK items each (deg > TCW_CHUNK)
+  const int64_t capwh = 2 * (nnz / TCW_CHUNK) + 64;
+  LAGR_TRY(alloc_n(&P->tc_listwh, (size_t)capwh, s, msg, "warp anchor items"));
+  P->tc_capwh = capwh;
   LAGR_TRY(alloc_n(&P->tc_listc, (size_t)capc, s, msg, "CTA anchors"));
   LAGR_TRY(alloc_n(&P->tc_scan, (size_t)scan_scratch_len(n), s, msg, "scan scratch"));
+  LAGR_TRY(alloc_n(&P->tc_rank, (size_t)n + 1, s, msg, "degree ranks"));
+  LAGR_TRY(alloc_n(&P->tc_sortbuf, 4 * (size_t)n + 4, s, msg, "rank sort buffers"));
+  LAGR_TRY(alloc_n(&P->tc_radix, (size_t)radix_scratch_len(n), s, msg, "radix scratch"));
+  LAGR_TRY(alloc_n(&P->tc_radix_scan, (size_t)scan_scratch_len(radix_scratch_len(n)), s, msg, "radix scan scratch"));
   P->tc_capc = capc;
   return LAGR_OK;
 }
@@ -548,35 +637,56 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
       tc_decide<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, n, xstar, P->dscal);
     }
     tc_set_mode<<<1, 1, 0, s>>>(n, method, P->dscal);
+    // ranks: the stable ascending-degree order (the relabelling of Alg. 6), or the ids
+    int32_t *keys = P->tc_sortbuf, *vals = keys + n, *tk = vals + n, *tv = tk + n;
+    tc_rank_keys<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, n, keys, vals);
+    LAGR_LAUNCH_CHECK();
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) bits++;
+    LAGR_TRY(radix_sort_pairs(keys, vals, tk, tv, n, bits, s, msg, P->tc_radix, P->tc_radix_scan));
+    tc_rank_scatter<<<grid_for(n, 256), 256, 0, s>>>(vals, n, P->dscal, P->tc_rank);
     const RowPlan &rp = P->pr_at;
-    tc_orient_rows<false><<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, G->row_degree, rp.blk, P->dscal, P->tc_dplus,
+    tc_orient_rows<false><<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, P->dscal, P->tc_dplus,
                                                    nullptr, nullptr, 0);
     if (rp.nheavy > 0)
-      tc_orient_count_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, G->row_degree, P->dscal, P->tc_dplus,
-                                                    rp.heavy, rp.nheavy);
+      tc_orient_count_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, P->tc_dplus, rp.heavy,
+                                                    rp.nheavy);
     LAGR_LAUNCH_CHECK();
     LAGR_TRY(exclusive_scan(P->tc_dplus, G->u_rowptr, n, s, msg, P->tc_scan));
-    tc_orient_rows<true><<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, G->row_degree, rp.blk, P->dscal, nullptr,
+    tc_orient_rows<true><<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, P->dscal, nullptr,
                                                   G->u_rowptr, G->u_colidx, ucap);
     if (rp.nheavy > 0)
-      tc_orient_fill_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, G->row_degree, P->dscal, G->u_rowptr,
+      tc_orient_fill_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, P->dscal, G->u_rowptr,
                                                    G->u_colidx, ucap, rp.heavy, rp.nheavy);
-    tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, P->tc_dplus, n, P->tc_listw, P->tc_listc, P->tc_capc,
-                                                 P->dscal, prm.wmax, prm.chunk);
+    tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, P->tc_dplus, n, P->tc_listw, P->tc_listwh,
+                                                 P->tc_capwh, P->tc_listc, P->tc_capc, P->dscal, prm.wmax,
+                                                 prm.chunk);
     LAGR_LAUNCH_CHECK();
   } else {
     static_assert(SL_QC == SL_QW + 1 && SL_TOTAL == SL_QC + 1, "slot layout");
     LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal + SL_QW, 0, 3 * sizeof(int64_t), s));
+    LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal + SL_QWL, 0, sizeof(int64_t), s));
   }
   if (counts != (unsigned long long *)(P->dscal + SL_TOTAL))
     LAGR_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ngraphs * sizeof(unsigned long long), s));
-  const size_t smem_c = TCC_SLOTS * sizeof(int32_t) + (1 << TCC_FILTER_BITS_LOG) / 8;
-  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-  tc_count_cta<<<152 * 4, TCC_THREADS, smem_c, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx, P->tc_dplus,
-                                                    P->tc_listc, P->dscal, voff, ngraphs, counts, prm.chunk,
-                                                    P->tc_capc);
-  tc_count_warp<<<152 * 8, TCW_WARPS * 32, 0, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx, P->tc_dplus,
-                                                   P->tc_listw, P->dscal, voff, ngraphs, counts);
+  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCC_SMEM));
+  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCW_SMEM));
+  // windows: the top ranks [n - window, n) (or all of them on small graphs)
+  const int32_t w0c = n > (1 << TCC_WIN_LOG) ? n - (1 << TCC_WIN_LOG) : 0;
+  const int32_t w0w = n > (1 << TCW_WIN_LOG) ? n - (1 << TCW_WIN_LOG) : 0;
+  {
+    KTimer kt(TK_TC_CTA, s);
+    tc_count_cta<<<152 * 4, TCC_THREADS, TCC_SMEM, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx, P->tc_dplus,
+                                                        P->tc_rank, P->tc_listc, P->dscal, w0c, voff, ngraphs, counts,
+                                                        prm.chunk, P->tc_capc);
+  }
+  {
+    KTimer kt(TK_TC_WARP, s);
+    tc_count_warp<<<152 * 4, TCW_WARPS * 32, TCW_SMEM, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx,
+                                                            P->tc_dplus, P->tc_rank, P->tc_listw, P->tc_listwh,
+                                                            P->tc_capwh, P->dscal, w0w,
+                                                            voff, ngraphs, counts);
+  }
   LAGR_LAUNCH_CHECK();
   return LAGR_OK;
 }

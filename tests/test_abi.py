@@ -136,3 +136,15 @@ def test_binding_fails_loudly_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError, match="CUDA"):
         L.Graph(torch.zeros(2, dtype=torch.int32), torch.zeros(1, dtype=torch.int32))
+
+
+def test_timing_api_host_side(lib):
+    import ctypes
+    ms, cnt = ctypes.c_double(-1.0), ctypes.c_int64(-1)
+    assert lib.lagr_timing_reset() == 0
+    assert lib.lagr_timing_read(b"no_such_kernel", ctypes.byref(ms), ctypes.byref(cnt)) == -2
+    assert lib.lagr_timing_read(None, ctypes.byref(ms), ctypes.byref(cnt)) == -1
+    for name in (b"pr_gather", b"tc_count_cta", b"tc_count_warp", b"bfs_push_small", b"bfs_push_lb", b"bfs_pull"):
+        assert lib.lagr_timing_read(name, ctypes.byref(ms), ctypes.byref(cnt)) == 0
+        assert ms.value == 0.0 and cnt.value == 0
+    assert lib.lagr_timing_enable(1) == 0 and lib.lagr_timing_enable(0) == 0

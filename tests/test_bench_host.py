@@ -51,3 +51,14 @@ def test_single_rank_identity():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.job_throughput(10.0, 1, 1000.0) == pytest.approx(10.0)
+
+
+def test_tc_algorithmic_bytes_small():
+    import bench
+    import gen
+    # K4 (no degree sort): U = the 6 pairs (u < v); d+ = 3, 2, 1, 0
+    # 4(n+1) + 4 m_L + sum over U edges of 8 + 4 d+(v) = 20 + 24 + 48 + 4 (2 + 1 + 0 + 1 + 0 + 0)
+    assert bench.tc_algorithmic_bytes(gen.complete(4)) == 108
+    # star with 5 leaves (n = 6): mean degree 5/3 is not above 4 * median 1, so no sort; the hub
+    # is vertex 0, U(0) = the 5 leaves (d+ 0 each): 5 edges of 8 bytes
+    assert bench.tc_algorithmic_bytes(gen.star(5)) == 4 * 7 + 4 * 5 + 8 * 5

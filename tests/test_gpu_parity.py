@@ -417,3 +417,98 @@ def test_graph_check(L, rmat12):
     Gok = L.Graph(torch.from_numpy(d.rowptr).cuda(), torch.from_numpy(d.colidx).cuda(), directed=True)
     L.lagr_graph_check(Gok)
     assert Gok.struct.a_pattern_is_symmetric == 0
+
+
+def test_bfs_batch64_push_pull_and_heavy_rows(L):
+    # a hub of degree 6000 (a row past the row-block limit) joined to an R-MAT graph: the first
+    # levels push, the wide ones pull, and the hub's row is scanned by the heavy-row CTAs
+    base = gen.rmat(13, 8, seed=41)
+    hub = base.n
+    rows = np.repeat(np.arange(base.n), np.diff(base.rowptr))
+    leaves = np.arange(0, 6000 * 2, 2) % base.n
+    src = np.concatenate([rows, np.full(leaves.size, hub)])
+    dst = np.concatenate([base.colidx, leaves])
+    g = gen.from_edges(base.n + 1, src, dst)
+    G = dev(L, g)
+    for srcs in ([hub], [0, hub, 5], list(gen.sources(g, 64, seed=3)), list(gen.sources(g, 37, seed=4))):
+        lv = L.lagr_bfs_batch64(G, [int(x) for x in srcs]).cpu().numpy()
+        for i, s in enumerate(srcs):
+            assert np.array_equal(lv[i], oracle.bfs(g, int(s))[0]), (i, s)
+
+
+@pytest.mark.parametrize("method", [0, 1, 2])
+def test_tc_beyond_the_rank_window(L, method):
+    # more vertices than the CTA kernel's window of ranks (2^17): entries below the window go to
+    # the hash table (or, for anchors with none there, need no lookup at all).  Without the degree
+    # order (method 2) a power-law hub keeps thousands of low labels and takes the slow scan path,
+    # so that case runs on the uniform graph only.
+    graphs = [gen.erdos_renyi(300000, 12, seed=6)]
+    if method != 2:
+        graphs.append(gen.rmat(18, 8, seed=5))
+    for g in graphs:
+        assert L.lagr_tc(dev(L, g), method) == oracle.tc(g), g.name
+
+
+def _offset_copy(torch, a, dtype):
+    """`a` on the device as a view that starts 4 bytes past a 16-byte boundary."""
+    buf = torch.empty(a.size + 1, dtype=dtype, device="cuda")
+    buf[1:] = torch.from_numpy(a).to("cuda")
+    v = buf[1:]
+    assert v.data_ptr() % 16 == 4
+    return v
+
+
+def test_pagerank_misaligned_csr(L):
+    # colidx / val not 16-byte aligned: the gather takes its scalar loads; same sums, same order
+    import torch
+    g = gen.rmat(13, 16, seed=41)
+    G = dev(L, g)
+    r_al, it_al = L.lagr_pagerank(G, 0.85, 0.0, 15)
+    Gm = L.Graph(torch.from_numpy(g.rowptr).to("cuda"), _offset_copy(torch, g.colidx, torch.int32))
+    r_mis, it_mis = L.lagr_pagerank(Gm, 0.85, 0.0, 15)
+    assert it_al == it_mis == 15
+    assert torch.equal(r_al, r_mis)
+    ro, _, _ = oracle.pagerank(g, 0.85, 0.0, 15)
+    pr_close(r_mis.cpu().numpy(), ro)
+    # the adjoint gathers over the rows of W with its values: misaligned colidx and val
+    gw = gen.rmat_weighted_directed(11, 16, seed=43)
+    w64 = gw.meta["val64"]
+    c = gen.normal(gw.n, 7)
+    ct = torch.tensor(c, dtype=torch.float32, device="cuda")
+    Gw = dev(L, gw)
+    Gwm = L.Graph(torch.from_numpy(gw.rowptr).to("cuda"), _offset_copy(torch, gw.colidx, torch.int32),
+                  _offset_copy(torch, gw.val, torch.float32), directed=True)
+    flags = L.LAGR_PR_WEIGHTED
+    r1, _ = L.lagr_pagerank(Gw, 0.85, 0.0, 60, flags=flags)
+    r2, _ = L.lagr_pagerank(Gwm, 0.85, 0.0, 60, flags=flags)
+    assert torch.equal(r1, r2)
+    dw1, dv1, _ = L.lagr_pagerank_backward(Gw, ct, r1, 0.85, 0.0, 80, flags=flags)
+    dw2, dv2, _ = L.lagr_pagerank_backward(Gwm, ct, r2, 0.85, 0.0, 80, flags=flags)
+    assert torch.equal(dw1, dw2) and torch.equal(dv1, dv2)
+    ro, _, _ = oracle.pagerank_weighted(gw, w64, None, 0.85, 1e-14, 5000)
+    dwo, _, _, _ = oracle.pagerank_adjoint(gw, w64, ro, c, None, 0.85, 1e-14, 5000)
+    assert rel_err(dw2.cpu().numpy(), dwo) <= 1e-3
+
+
+def test_kernel_timing_counts_launches(L, rmat12):
+    import torch
+    G = dev(L, rmat12)
+    L.timing_reset()
+    L.timing_enable(True)
+    try:
+        _, it = L.lagr_pagerank(G, 0.85, 0.0, 7)
+        t = L.lagr_tc(G, L.LAGR_TC_AUTO)
+        L.lagr_bfs(G, 0, 0, level=torch.empty(rmat12.n, dtype=torch.int32, device="cuda"))
+    finally:
+        L.timing_enable(False)
+    ms, cnt = L.timing_read("pr_gather")
+    assert it == 7 and cnt == 7 and ms > 0.0
+    for k in ("tc_count_cta", "tc_count_warp"):
+        ms, cnt = L.timing_read(k)
+        assert cnt == 1 and ms > 0.0
+    assert sum(L.timing_read(k)[1] for k in ("bfs_push_small", "bfs_push_lb", "bfs_pull")) >= 1
+    assert t == oracle.tc(rmat12)
+    # nothing is recorded once timing is off
+    L.timing_reset()
+    L.lagr_pagerank(G, 0.85, 0.0, 3)
+    assert L.timing_read("pr_gather") == (0.0, 0)
