@@ -73,29 +73,70 @@ __device__ __forceinline__ bool claim(uint32_t *__restrict__ visited, int32_t v)
   return !(atomicOr(&visited[v >> 5], bit) & bit);
 }
 
-// One push level over the frontier qin[0..nq): warps take 32 frontier vertices at a time.
-// Appends to qout through *qcount; adds the out-degree of every discovered vertex to *mcount.
-__device__ __forceinline__ void push_level(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                           const int32_t *__restrict__ qin, int64_t nq, int32_t *__restrict__ qout,
-                                           uint32_t *__restrict__ visited, int32_t *__restrict__ level,
-                                           int32_t *__restrict__ parent, int32_t lev, int64_t warp0, int64_t nwarps,
-                                           unsigned long long *qcount, unsigned long long &mdeg) {
+// One push level of the single-CTA kernel.  Frontier vertices with at most NARROW_DEG edges are
+// taken one per thread, whose column and visited loads are all in flight together (a narrow level
+// is a chain of dependent loads, so their latency, not bandwidth, is its cost); longer rows are
+// listed in big[] and walked afterwards by the warps, 32 edges at a time.  Appends to qout through
+// *qcount; adds the out-degree of every discovered vertex to mdeg.
+constexpr int NARROW_DEG = 8;
+__device__ __forceinline__ void push_level_narrow(const int32_t *__restrict__ rowptr,
+                                                  const int32_t *__restrict__ colidx, const int32_t *__restrict__ qin,
+                                                  int64_t nq, int32_t *__restrict__ qout,
+                                                  uint32_t *__restrict__ visited, int32_t *__restrict__ level,
+                                                  int32_t *__restrict__ parent, int32_t lev,
+                                                  unsigned long long *qcount, unsigned long long &mdeg, int32_t *big,
+                                                  int *nbig) {
+  for (int64_t i = threadIdx.x; i < nq; i += blockDim.x) {
+    const int32_t u = qin[i];
+    const int32_t st = rowptr[u];
+    int32_t len = rowptr[u + 1] - st;
+    if (len > NARROW_DEG) {
+      big[atomicAdd(nbig, 1)] = u;
+      len = 0;
+    }
+    int32_t v[NARROW_DEG];
+#pragma unroll
+    for (int j = 0; j < NARROW_DEG; j++) v[j] = j < len ? colidx[st + j] : -1;
+    uint32_t fresh = 0;  // bit j: candidate v[j] exists and is not yet visited
+#pragma unroll
+    for (int j = 0; j < NARROW_DEG; j++)
+      if (v[j] >= 0 && !((visited[v[j] >> 5] >> (v[j] & 31)) & 1u)) fresh |= 1u << j;
+    while (fresh) {
+      const int j = __ffs(fresh) - 1;
+      fresh &= fresh - 1;
+      int32_t w = v[0];
+#pragma unroll
+      for (int q = 1; q < NARROW_DEG; q++)
+        if (q == j) w = v[q];
+      const int32_t dw = rowptr[w + 1] - rowptr[w];  // issued with the claim below
+      if (!(atomicOr(&visited[w >> 5], 1u << (w & 31)) & (1u << (w & 31)))) {
+        qout[atomicAdd(qcount, 1ull)] = w;
+        if (level) level[w] = lev;
+        if (parent) parent[w] = u;
+        mdeg += (unsigned long long)dw;
+      }
+    }
+  }
+  __syncthreads();
+  // the longer rows: warps take 32 of them at a time and spread their edges over the lanes
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-  for (int64_t wb = warp0 * 32; wb < nq; wb += nwarps * 32) {
-    const int64_t i = wb + lane;
+  const int nb = *nbig;
+  for (int wb = (threadIdx.x >> 5) * 32; wb < nb; wb += (int)(blockDim.x >> 5) * 32) {
     int32_t u = -1, st = 0, len = 0;
-    if (i < nq) {
-      u = qin[i];
+    if (wb + lane < nb) {
+      u = big[wb + lane];
       st = rowptr[u];
       len = rowptr[u + 1] - st;
     }
     warp_segments(st, len, u, [&](bool valid, int uu, int, int gidx) {
       bool won = false;
-      int32_t v = 0;
+      int32_t w = 0;
+      int32_t dw = 0;
       if (valid) {
-        v = colidx[gidx];
-        won = claim(visited, v);
+        w = colidx[gidx];
+        won = claim(visited, w);
+        if (won) dw = rowptr[w + 1] - rowptr[w];
       }
       const unsigned m = __ballot_sync(LAGR_FULL_MASK, won);
       if (m) {
@@ -103,10 +144,10 @@ __device__ __forceinline__ void push_level(const int32_t *__restrict__ rowptr, c
         if (lane == 0) pos = atomicAdd(qcount, (unsigned long long)__popc(m));
         pos = __shfl_sync(LAGR_FULL_MASK, pos, 0);
         if (won) {
-          qout[pos + __popc(m & lt)] = v;
-          if (level) level[v] = lev;
-          if (parent) parent[v] = uu;
-          mdeg += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+          qout[pos + __popc(m & lt)] = w;
+          if (level) level[w] = lev;
+          if (parent) parent[w] = uu;
+          mdeg += (unsigned long long)dw;
         }
       }
     });
@@ -256,15 +297,16 @@ __global__ void __launch_bounds__(256)
 
 // Many narrow push levels in one CTA.  Returns when the frontier is empty, grows past SMALL_MAX
 // vertices or SMALL_EDGES out-edges, the direction rule asks for a pull, or max_level is reached.
-__global__ void __launch_bounds__(SMALL_THREADS)
+__global__ void __launch_bounds__(SMALL_THREADS, 1)
     bfs_push_small(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
                    int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
                    int32_t *__restrict__ parent, int64_t *__restrict__ c, int32_t max_level, int allow_pull) {
   __shared__ unsigned long long s_next, s_mdeg;
+  __shared__ int32_t s_big[SMALL_MAX];  // frontier vertices with long rows (the caller keeps nq <= SMALL_MAX)
+  __shared__ int s_nbig;
   int64_t nq = c[B_NQ], mu = c[B_MU], mf = c[B_MF];
   int32_t lev = (int32_t)c[B_LEV];
   int par = (int)c[B_PAR];
-  const int64_t warp0 = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int exit_reason = 0;
   bool first = true, growing = false;
   for (;;) {
@@ -279,12 +321,13 @@ __global__ void __launch_bounds__(SMALL_THREADS)
     if (threadIdx.x == 0) {
       s_next = 0;
       s_mdeg = 0;
+      s_nbig = 0;
     }
     __syncthreads();
     const int32_t *qin = par ? qb : qa;
     int32_t *qout = par ? qa : qb;
     unsigned long long mdeg = 0;
-    push_level(rowptr, colidx, qin, nq, qout, visited, level, parent, lev + 1, warp0, nwarps, &s_next, mdeg);
+    push_level_narrow(rowptr, colidx, qin, nq, qout, visited, level, parent, lev + 1, &s_next, mdeg, s_big, &s_nbig);
     mdeg = warp_sum(mdeg);
     if ((threadIdx.x & 31) == 0 && mdeg) atomicAdd(&s_mdeg, mdeg);
     __syncthreads();

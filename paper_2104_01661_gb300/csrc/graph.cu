@@ -107,7 +107,7 @@ void priv_release(lagr_graph G, cudaStream_t s) {
   Priv *P = static_cast<Priv *>(G->priv);
   if (!P) return;
   free_tc_cache(P, s);
-  for (RowPlan *rp : {&P->pr_at, &P->pr_a}) {
+  for (RowPlan *rp : {&P->pr_at, &P->pr_a, &P->pr_fwd, &P->pr_adj}) {
     dev_free(rp->blk, s);
     dev_free(rp->heavy, s);
     dev_free(rp->hc_off, s);

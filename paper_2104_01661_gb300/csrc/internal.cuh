@@ -98,6 +98,7 @@ struct RowPlan {
   int32_t *hc_row = nullptr;  // [nhc]
   int32_t nhc = 0;
   uint8_t *hblk = nullptr;    // [nblk] 1 where the block is one heavy row (every heavy row is a block of its own)
+  int32_t units = 0, heavy_len = 0, hchunk = 0;  // the plan's block size, heavy-row threshold and chunk
 };
 constexpr int ROW_HCHUNK = 8192;
 
@@ -117,8 +118,10 @@ struct Priv {
   int64_t tc_capc = 0;
   int2 *tc_listwh = nullptr;  // warp items of the warp anchors with many neighbours
   int64_t tc_capwh = 0;
-  // row plans of the PageRank gathers over the rows of A' (forward) and of A (adjoint)
-  RowPlan pr_at, pr_a;
+  // row plans: over the rows of A' (shared by the triangle orientation and the 64-source BFS pull)
+  // and of A (the adjoint's edge gradient), in blocks of ROW_UNITS; and the finer plans of the
+  // PageRank gathers (blocks of one warp's work) over A' (forward) and A (adjoint)
+  RowPlan pr_at, pr_a, pr_fwd, pr_adj;
 };
 
 enum ScalarSlot {
@@ -132,6 +135,7 @@ enum ScalarSlot {
   SC_COUNT6 = 7,
   SC_COUNT7 = 8,
   SC_COUNT8 = 9,
+  SC_COUNT9 = 10,
   LAGR_NSCAL = 16,
   LAGR_NHOST = 64  // int64 slots of the pinned host mirror (also stages up to 64 int32 sources)
 };
@@ -139,7 +143,8 @@ enum ScalarSlot {
 int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out);
 
 // build (once; no-op when pl->nblk >= 0) the row plan of a CSR.  Synchronises the stream.
-int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg);
+int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg, int32_t units = ROW_UNITS,
+             int32_t heavy = ROW_HEAVY, int32_t hchunk = ROW_HCHUNK);
 
 // Opt-in device timing of the hot kernels (lagr_timing_*): construct a KTimer right before a
 // launch and let it go out of scope right after; it records an event pair on the stream when

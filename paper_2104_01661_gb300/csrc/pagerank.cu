@@ -21,6 +21,7 @@
 // MODE 2: adjoint (rows of W)   l'_i = g_i + damping sum_j W(i,j) l_j [+ damping (v.l) if i dangling]
 // where c = (1 - damping) [+ damping * (dangling mass of t) with LAGR_PR_DANGLING].
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 
 #include "internal.cuh"
@@ -29,18 +30,28 @@ namespace lagr {
 namespace {
 
 constexpr int PR_THREADS = 256;
-constexpr int PR_UNITS = ROW_UNITS;                 // units (entries + rows) per row block
+constexpr int PR_UNITS = ROW_UNITS;                 // units (entries + rows) per edge-gradient block
+constexpr int PR_WUNITS = 1024;   // units per block of the gathers' row plans (one warp's work item)
+constexpr int PR_WHEAVY = 1024;   // longer rows are cut into chunks of PR_WHCHUNK entries
+constexpr int PR_WHCHUNK = 2048;
 constexpr int PR_CHUNK = 8;                         // iterations launched between host checks
 constexpr int PR_INIT_BLOCKS = 152 * 8;
 
+constexpr int PR_FIN_BLOCKS = 32;  // CTAs of the partial-sum fold
+
 struct PrState {
+  // read by the host (the first PR_STATE_HOST bytes)
   double resid;   // last L1 change
   double aux;     // last auxiliary sum (dangling mass, or v . lambda)
   float coef;     // scalar for the next iteration (see the file comment)
   int done;       // set once the tolerance is met or itermax reached
   int iters;      // iterations done
-  int pad;
+  int queue;      // next row block of the running gather (reset by pr_finalize)
+  // device only: the fold's per-CTA sums and its arrival counter
+  double2 fold[PR_FIN_BLOCKS];
+  unsigned int arrive;
 };
+constexpr size_t PR_STATE_HOST = 32;  // resid, aux, coef, done, iters, queue
 
 // per-vertex damping / out-degree (0 for dangling rows) from the rows of A
 __global__ void pr_scale(const int32_t *__restrict__ rowptr, int32_t n, float damping, float *__restrict__ sc) {
@@ -90,7 +101,7 @@ struct IterArgs {
 
 template <int MODE>
 __device__ __forceinline__ float gather_one(const IterArgs &a, int32_t k) {
-  const int32_t j = __ldg(&a.colidx[k]);
+  const int32_t j = __ldg(a.colidx + k);
   if (MODE == 0) return __ldg(&a.x[j]);
   return __ldg(&a.val[k]) * __ldg(&a.x[j]);
 }
@@ -130,15 +141,15 @@ __device__ __forceinline__ void row_out(const IterArgs &a, int32_t i, float acc,
 
 constexpr int PR_EPL = 8;                  // entries per lane per step
 constexpr int PR_STEP = 32 * PR_EPL;       // entries per warp step
-constexpr int PR_WARPS = PR_THREADS / 32;  // row blocks per CTA
 
 // the column indices (and values) of entries k .. k + PR_EPL - 1; those outside [lo, hi) read as -1
 template <int MODE>
 __device__ __forceinline__ void load_step(const IterArgs &a, int32_t k, int32_t lo, int32_t hi, int32_t (&c)[PR_EPL],
                                           float (&v)[PR_EPL]) {
+  const int32_t *__restrict__ cols = a.colidx;
   if (a.vec && k >= 0 && k + PR_EPL <= hi) {
-    const int4 c0 = __ldg(reinterpret_cast<const int4 *>(a.colidx + k));
-    const int4 c1 = __ldg(reinterpret_cast<const int4 *>(a.colidx + k + 4));
+    const int4 c0 = __ldg(reinterpret_cast<const int4 *>(cols + k));
+    const int4 c1 = __ldg(reinterpret_cast<const int4 *>(cols + k + 4));
     c[0] = c0.x; c[1] = c0.y; c[2] = c0.z; c[3] = c0.w;
     c[4] = c1.x; c[5] = c1.y; c[6] = c1.z; c[7] = c1.w;
     if (MODE != 0) {
@@ -154,62 +165,43 @@ __device__ __forceinline__ void load_step(const IterArgs &a, int32_t k, int32_t 
 #pragma unroll
     for (int j = 0; j < PR_EPL; j++) {
       const bool ok = k + j >= lo && k + j < hi;
-      c[j] = ok ? __ldg(a.colidx + k + j) : -1;
+      c[j] = ok ? __ldg(cols + k + j) : -1;
       if (MODE != 0) v[j] = ok ? __ldg(a.val + k + j) : 0.0f;
     }
   }
 }
 
-// last row i in [lo, hi] with rowptr[i] <= k (rowptr[lo] <= k holds)
-__device__ __forceinline__ int32_t row_of(const int32_t *__restrict__ rowptr, int32_t lo, int32_t hi, int32_t k) {
+__device__ __forceinline__ float gather_x(const IterArgs &a, int32_t c) {
+  return c < 0 ? 0.0f : __ldg(a.x + c);
+}
+
+// last row index q in [lo, hi] with rp[q] <= k (rp[lo] <= k holds); rp in shared memory
+__device__ __forceinline__ int32_t srow_of(const int32_t *rp, int32_t lo, int32_t hi, int32_t k) {
   while (lo < hi) {
     const int32_t mid = (lo + hi + 1) >> 1;
-    if (__ldg(rowptr + mid) <= k) lo = mid; else hi = mid - 1;
+    if (rp[mid] <= k) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
 
+// one row block (at most PR_WUNITS units), one warp: writes the block's partials.  srp: this
+// warp's shared-memory copy of the block's row pointers.
 template <int MODE>
-__global__ void __launch_bounds__(PR_THREADS)
-    pr_warp(IterArgs a, const int32_t *__restrict__ blk, int32_t nblk, const uint8_t *__restrict__ hblk,
-            const int32_t *__restrict__ heavy, const int32_t *__restrict__ hc_off, const int32_t *__restrict__ hc_row,
-            const PrState *__restrict__ st, double2 *__restrict__ partials) {
-  __shared__ float red[32];
-  if (st->done) return;  // uniform over the grid
-  const float coef = st->coef;
-  const int32_t nwb = (nblk + PR_WARPS - 1) / PR_WARPS;  // CTAs of row blocks
-  if ((int32_t)blockIdx.x >= nwb) {
-    // the trailing CTAs each sum one chunk of ROW_HCHUNK entries of a row longer than ROW_HEAVY,
-    // while the row blocks are still being processed; pr_heavy_finish adds the chunks up
-    const int32_t cidx = blockIdx.x - nwb;
-    const int32_t h = hc_row[cidx];
-    const int32_t i = heavy[h];
-    const int32_t b = a.rowptr[i] + (cidx - hc_off[h]) * ROW_HCHUNK;
-    const int32_t e = min(a.rowptr[i + 1], b + ROW_HCHUNK);
-    float acc = 0.0f;
-    int32_t k = b + threadIdx.x;
-    for (; k + 3 * PR_THREADS < e; k += 4 * PR_THREADS) {
-      const float g0 = gather_one<MODE>(a, k), g1 = gather_one<MODE>(a, k + PR_THREADS);
-      const float g2 = gather_one<MODE>(a, k + 2 * PR_THREADS), g3 = gather_one<MODE>(a, k + 3 * PR_THREADS);
-      acc += (g0 + g1) + (g2 + g3);
-    }
-    for (; k < e; k += PR_THREADS) acc += gather_one<MODE>(a, k);
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) a.hpart[cidx] = acc;
-    return;
-  }
+__device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const int32_t *__restrict__ blk,
+                                           const uint8_t *__restrict__ hblk, int32_t wb,
+                                           double2 *__restrict__ partials, int32_t *srp) {
   const int lane = threadIdx.x & 31;
-  const int32_t wb = blockIdx.x * PR_WARPS + (threadIdx.x >> 5);
-  if (wb >= nblk) return;
   const int32_t r0 = blk[wb], r1 = blk[wb + 1];
-  const int32_t *__restrict__ rowptr = a.rowptr;
+  const int32_t nr = r1 - r0;
   double resid = 0.0, aux = 0.0;
-  if (!hblk[wb]) {  // (a block that is one heavy row is summed by the chunk CTAs)
-    for (int32_t i = r0 + lane; i < r1; i += 32)  // empty rows
-      if (__ldg(rowptr + i) == __ldg(rowptr + i + 1)) row_out<MODE>(a, i, 0.0f, coef, resid, aux);
-    const int32_t e0 = __ldg(rowptr + r0), e1 = __ldg(rowptr + r1);
+  if (!hblk[wb]) {  // (a block that is one heavy row is summed by the chunk items)
+    for (int32_t q = lane; q <= nr; q += 32) srp[q] = __ldg(a.rowptr + r0 + q);
+    __syncwarp();
+    for (int32_t q = lane; q < nr; q += 32)  // empty rows
+      if (srp[q] == srp[q + 1]) row_out<MODE>(a, r0 + q, 0.0f, coef, resid, aux);
+    const int32_t e0 = srp[0], e1 = srp[nr];
     const int32_t kb = e0 & ~3;  // steps start 16-byte aligned
-    int32_t rc = r0;             // the row holding the first entry of the current step
+    int32_t rc = 0;              // the block row holding the first entry of the current step
     float carry = 0.0f;          // the open part of the row running into the current step
     int32_t cn[PR_EPL];
     float vn[PR_EPL];
@@ -219,20 +211,20 @@ __global__ void __launch_bounds__(PR_THREADS)
       float g[PR_EPL];
 #pragma unroll
       for (int j = 0; j < PR_EPL; j++) {
-        const float xv = cn[j] >= 0 ? __ldg(a.x + cn[j]) : 0.0f;
+        const float xv = gather_x(a, cn[j]);
         g[j] = MODE == 0 ? xv : vn[j] * xv;
       }
       if (gs + PR_STEP < e1) load_step<MODE>(a, k0 + PR_STEP, e0, e1, cn, vn);
       // this lane's entries [ks, ke)
       const int32_t ks = max(k0, e0), ke = min(k0 + PR_EPL, e1);
-      float v = 0.0f;     // open part of the lane's last row (passed on by the scan)
-      bool fresh = false;  // the scan restarts at this lane (nothing open flows through it)
+      float v = 0.0f;       // open part of the lane's last row (passed on by the scan)
+      bool fresh = false;   // the scan restarts at this lane (nothing open flows through it)
       bool hclose = false;  // the lane closes a row that began before it (needs the joined prefix)
       float hsum = 0.0f;
       int32_t hrow = 0;
       if (ks < ke) {
-        int32_t row = row_of(rowptr, rc, r1 - 1, ks);
-        int32_t rs = __ldg(rowptr + row), re = __ldg(rowptr + row + 1);
+        int32_t q = srow_of(srp, rc, nr - 1, ks);
+        int32_t rs = srp[q], re = srp[q + 1];
         const bool open_head = rs < ks;
         bool first = true;
         float acc = 0.0f;
@@ -245,16 +237,16 @@ __global__ void __launch_bounds__(PR_THREADS)
               if (first && open_head) {
                 hclose = true;
                 hsum = acc;
-                hrow = row;
+                hrow = q;
               } else {
-                row_out<MODE>(a, row, acc, coef, resid, aux);
+                row_out<MODE>(a, r0 + q, acc, coef, resid, aux);
               }
             }
             first = false;
             acc = 0.0f;
-            row++;
+            q++;
             rs = re;
-            re = __ldg(rowptr + row + 1);
+            re = srp[q + 1];
           }
           acc += g[j];
         }
@@ -262,9 +254,9 @@ __global__ void __launch_bounds__(PR_THREADS)
           if (first && open_head) {
             hclose = true;
             hsum = acc;
-            hrow = row;
+            hrow = q;
           } else {
-            row_out<MODE>(a, row, acc, coef, resid, aux);
+            row_out<MODE>(a, r0 + q, acc, coef, resid, aux);
           }
           fresh = true;
         } else {
@@ -287,19 +279,68 @@ __global__ void __launch_bounds__(PR_THREADS)
       if (!sf) sv += carry;
       float before = __shfl_up_sync(LAGR_FULL_MASK, sv, 1);
       if (lane == 0) before = carry;
-      if (hclose) row_out<MODE>(a, hrow, before + hsum, coef, resid, aux);
+      if (hclose) row_out<MODE>(a, r0 + hrow, before + hsum, coef, resid, aux);
       carry = __shfl_sync(LAGR_FULL_MASK, sv, 31);
       // the next step starts inside the row that holds this step's last entry
-      const int32_t klast = min(gs + PR_STEP, e1) - 1;
-      rc = row_of(rowptr, rc, r1 - 1, klast);
+      rc = srow_of(srp, rc, nr - 1, min(gs + PR_STEP, e1) - 1);
     }
+    __syncwarp();  // srp is rewritten by the warp's next block
   }
   resid = warp_sum(resid);
   aux = warp_sum(aux);
   if (lane == 0) partials[wb] = make_double2(resid, aux);
 }
 
-// the rows longer than ROW_HEAVY: add each row's chunk sums in chunk order, then the row's output
+// one chunk of hchunk entries of a heavy row, one warp: its sum in hpart[cidx] (pr_heavy_finish
+// adds a row's chunks up in chunk order)
+template <int MODE>
+__device__ __forceinline__ void warp_chunk(const IterArgs &a, const int32_t *__restrict__ heavy,
+                                           const int32_t *__restrict__ hc_off, const int32_t *__restrict__ hc_row,
+                                           int32_t hchunk, int32_t cidx) {
+  const int lane = threadIdx.x & 31;
+  const int32_t h = hc_row[cidx];
+  const int32_t i = heavy[h];
+  const int32_t b = __ldg(a.rowptr + i) + (cidx - hc_off[h]) * hchunk;
+  const int32_t e = min(__ldg(a.rowptr + i + 1), b + hchunk);
+  float acc = 0.0f;
+  for (int32_t gs = b & ~3; gs < e; gs += PR_STEP) {
+    int32_t c[PR_EPL];
+    float v[PR_EPL];
+    load_step<MODE>(a, gs + PR_EPL * lane, b, e, c, v);
+#pragma unroll
+    for (int j = 0; j < PR_EPL; j++) {
+      const float xv = gather_x(a, c[j]);
+      acc += MODE == 0 ? xv : v[j] * xv;
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) a.hpart[cidx] = acc;
+}
+
+// Persistent CTAs: their warps take work items from one queue until none is left: first the
+// chunks of the heavy rows, then the row blocks.
+template <int MODE>
+__global__ void __launch_bounds__(PR_THREADS, MODE == 0 ? 5 : 4)
+    pr_warp(IterArgs a, const int32_t *__restrict__ blk, int32_t nblk, const uint8_t *__restrict__ hblk,
+            const int32_t *__restrict__ heavy, const int32_t *__restrict__ hc_off, const int32_t *__restrict__ hc_row,
+            int32_t nhc, int32_t hchunk, PrState *__restrict__ st, double2 *__restrict__ partials) {
+  __shared__ int32_t s_rp[PR_THREADS / 32][PR_WUNITS + 2];  // each warp's row pointers
+  if (st->done) return;  // uniform over the grid
+  const float coef = st->coef;
+  const int lane = threadIdx.x & 31;
+  int32_t *srp = s_rp[threadIdx.x >> 5];
+  const int32_t nitems = nhc + nblk;
+  for (;;) {
+    int32_t q = 0;
+    if (lane == 0) q = atomicAdd(&st->queue, 1);
+    q = __shfl_sync(LAGR_FULL_MASK, q, 0);
+    if (q >= nitems) break;
+    if (q < nhc) warp_chunk<MODE>(a, heavy, hc_off, hc_row, hchunk, q);
+    else warp_block<MODE>(a, coef, blk, hblk, q - nhc, partials, srp);
+  }
+}
+
+// the heavy rows: add each row's chunk sums in chunk order, then the row's output
 constexpr int PR_HF_THREADS = 256;
 template <int MODE>
 __global__ void __launch_bounds__(PR_HF_THREADS)
@@ -321,28 +362,51 @@ __global__ void __launch_bounds__(PR_HF_THREADS)
 }
 
 // fold the partials in a fixed order; init != 0 only prepares the first coefficient
-__global__ void pr_finalize(const double2 *__restrict__ partials, int np, PrState *__restrict__ st, int mode,
-                            float damping, int dangling, double tol, int itermax, int init) {
+// Fold the partials in a fixed order: CTA b sums the b-th contiguous share (a fixed tree), and the
+// CTA that arrives last adds the PR_FIN_BLOCKS sums in order and updates the state (the result does
+// not depend on which CTA is last).  init != 0 only prepares the first coefficient.
+constexpr int PR_FIN_THREADS = 512;
+__global__ void __launch_bounds__(PR_FIN_THREADS)
+    pr_finalize(const double2 *__restrict__ partials, int np, PrState *__restrict__ st, int mode, float damping,
+                int dangling, double tol, int itermax, int init) {
   __shared__ double red[32];
-  if (!init && st->done) return;
+  __shared__ bool last;
+  if (!init && st->done) return;  // uniform: done changes only at the end of a fold
+  const int per = (np + PR_FIN_BLOCKS - 1) / PR_FIN_BLOCKS;
+  const int lo = blockIdx.x * per, hi = min(np, lo + per);
   double r = 0.0, a = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     r += partials[i].x;
     a += partials[i].y;
   }
   r = block_sum(r, red);
   a = block_sum(a, red);
   if (threadIdx.x == 0) {
-    float coef;
-    if (mode == 2) coef = dangling ? (float)((double)damping * a) : 0.0f;
-    else coef = (float)((1.0 - (double)damping) + (dangling ? (double)damping * a : 0.0));
-    st->coef = coef;
-    st->aux = a;
-    if (!init) {
-      st->iters += 1;
-      st->resid = r;
-      if (r < tol || st->iters >= itermax) st->done = 1;
-    }
+    st->fold[blockIdx.x] = make_double2(r, a);
+    __threadfence();
+    last = atomicAdd(&st->arrive, 1u) == PR_FIN_BLOCKS - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  r = 0.0;
+  a = 0.0;
+  for (int b = 0; b < PR_FIN_BLOCKS; b++) {
+    const volatile double *f = reinterpret_cast<volatile double *>(&st->fold[b]);
+    r += f[0];
+    a += f[1];
+  }
+  float coef;
+  if (mode == 2) coef = dangling ? (float)((double)damping * a) : 0.0f;
+  else coef = (float)((1.0 - (double)damping) + (dangling ? (double)damping * a : 0.0));
+  st->coef = coef;
+  st->aux = a;
+  st->queue = 0;  // the next gather starts its row-block queue afresh
+  st->arrive = 0;
+  if (!init) {
+    st->iters += 1;
+    st->resid = r;
+    if (r < tol || st->iters >= itermax) st->done = 1;
   }
 }
 
@@ -401,35 +465,52 @@ static inline int aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 template <int MODE>
 static void launch_iter(const RowPlan &pl, const IterArgs &a, PrState *st, double2 *partials, int32_t itermax,
                         double tol, cudaStream_t s) {
-  const int32_t nwb = (pl.nblk + PR_WARPS - 1) / PR_WARPS;
+  // as many persistent CTAs as can be resident at once (no more than there are warp items)
+  static int resident[3] = {0, 0, 0};
+  if (resident[MODE] == 0) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr_warp<MODE>, PR_THREADS, 0);
+    resident[MODE] = (per_sm > 0 && nsm > 0) ? per_sm * nsm : 152;
+  }
+  const int64_t items = (int64_t)pl.nhc + pl.nblk;
+  const int64_t need = (items * 32 + PR_THREADS - 1) / PR_THREADS;
+  const int grid = (int)(need < resident[MODE] ? (need > 0 ? need : 1) : resident[MODE]);
   {
     KTimer kt(TK_PR_GATHER, s);
-    pr_warp<MODE><<<nwb + pl.nhc, PR_THREADS, 0, s>>>(a, pl.blk, pl.nblk, pl.hblk, pl.heavy, pl.hc_off, pl.hc_row,
-                                                      st, partials);
+    pr_warp<MODE><<<grid, PR_THREADS, 0, s>>>(a, pl.blk, pl.nblk, pl.hblk, pl.heavy, pl.hc_off, pl.hc_row, pl.nhc,
+                                              pl.hchunk, st, partials);
   }
   const int hfb = heavy_finish_blocks(pl);
   if (hfb > 0)
     pr_heavy_finish<MODE><<<hfb, PR_HF_THREADS, 0, s>>>(a, pl.heavy, pl.nheavy, pl.hc_off, st, partials + pl.nblk);
   // fold exactly the slots written above (the rest may hold the init kernel's partials)
-  pr_finalize<<<1, 1024, 0, s>>>(partials, pl.nblk + hfb, st, MODE, a.damping, a.dangling, tol, itermax, 0);
+  pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials, pl.nblk + hfb, st, MODE, a.damping, a.dangling, tol,
+                                                       itermax, 0);
 }
 
 // start vector, w0 and the first coefficient (the init partials use the first PR_INIT_BLOCKS slots)
 static void launch_init(int mode, int32_t n, float *x, float *w, const float *sc, const float *src, const float *vvec,
                         float vuni, PrState *st, double2 *partials, float damping, int dangling, int32_t itermax,
                         double tol, cudaStream_t s) {
-  if (mode == 2) pr_init<2><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
-  else if (mode == 1) pr_init<1><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
-  else pr_init<0><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, w, sc, src, vvec, vuni, partials);
-  pr_finalize<<<1, 1024, 0, s>>>(partials, PR_INIT_BLOCKS, st, mode, damping, dangling, tol, itermax, 1);
+  if (mode == 2)
+    pr_init<2><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
+  else if (mode == 1)
+    pr_init<1><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
+  else
+    pr_init<0><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, w, sc, src, vvec, vuni, partials);
+  pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials, PR_INIT_BLOCKS, st, mode, damping, dangling, tol,
+                                                       itermax, 1);
 }
 
 // Run the iteration of `mode` to convergence.  buf0 holds the start vector on entry (MODE 0/1,
 // written here unless warm) and the result on exit.  Returns the iteration count in *iters.
 static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const int32_t *rowptr, const int32_t *colidx,
-                    const float *val, float *buf0, const float *sc, const float *vvec, const float *gvec,
-                    const float *warm, float damping, float tol, int32_t itermax, int dangling, PrState *st,
-                    int32_t *iters, double *resid, cudaStream_t s, char *msg) {
+                    const float *val, float *buf0, const float *sc,
+                    const float *vvec, const float *gvec, const float *warm, float damping, float tol,
+                    int32_t itermax, int dangling, PrState *st, int32_t *iters, double *resid, cudaStream_t s,
+                    char *msg) {
   const int32_t n = G->n;
   const int vec = aligned16(colidx) && (val == nullptr || aligned16(val));
   Temp<float> buf1(s), w0(s), w1(s), hpart(s);
@@ -462,17 +543,21 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const in
         a.x = w[(k - 1) & 1];
         a.wout = w[k & 1];
         launch_iter<0>(pl, a, st, partials.p, itermax, (double)tol, s);
+      } else if (mode == 1) {
+        a.x = x[(k - 1) & 1];
+        launch_iter<1>(pl, a, st, partials.p, itermax, (double)tol, s);
       } else {
         a.x = x[(k - 1) & 1];
-        if (mode == 1) launch_iter<1>(pl, a, st, partials.p, itermax, (double)tol, s);
-        else launch_iter<2>(pl, a, st, partials.p, itermax, (double)tol, s);
+        launch_iter<2>(pl, a, st, partials.p, itermax, (double)tol, s);
       }
     }
     LAGR_LAUNCH_CHECK();
     launched += chunk;
-    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, st, sizeof(PrState), cudaMemcpyDeviceToHost, s));
+    static_assert(PR_STATE_HOST == offsetof(PrState, fold) && PR_STATE_HOST <= LAGR_NHOST * sizeof(int64_t),
+                  "host part of the state");
+    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, st, PR_STATE_HOST, cudaMemcpyDeviceToHost, s));
     LAGR_CUDA_TRY(cudaStreamSynchronize(s));
-    memcpy(&host, P->hscal, sizeof(PrState));
+    memcpy(&host, P->hscal, PR_STATE_HOST);
     if (host.done) break;
   }
   if (host.iters & 1) LAGR_CUDA_TRY(cudaMemcpyAsync(buf0, x[1], (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -520,21 +605,21 @@ int pr_plan_create(PrPlan **out, lagr_graph G, Priv *P, float damping, const flo
                    char *msg) {
   *out = nullptr;
   LAGR_TRY(lagr_property_AT(G, s, msg));
-  LAGR_TRY(row_plan(&P->pr_at, G->at_rowptr, G->n, s, msg));
+  LAGR_TRY(row_plan(&P->pr_fwd, G->at_rowptr, G->n, s, msg, PR_WUNITS, PR_WHEAVY, PR_WHCHUNK));
   PrPlan *pl = new PrPlan();
   pl->n = G->n;
   pl->rowptr = G->at_rowptr;
   pl->colidx = G->at_colidx;
-  pl->rows = P->pr_at;
+  pl->rows = P->pr_fwd;
   pl->vvec = vvec;
   pl->damping = damping;
-  pl->np = n_partials(P->pr_at);
+  pl->np = n_partials(P->pr_fwd);
   int st = alloc_n(&pl->sc, (size_t)G->n, s, msg, "PageRank scale");
   if (st == LAGR_OK) st = alloc_n(&pl->x1, (size_t)G->n, s, msg, "PageRank work vector");
   if (st == LAGR_OK) st = alloc_n(&pl->w0, (size_t)G->n, s, msg, "PageRank w");
   if (st == LAGR_OK) st = alloc_n(&pl->w1, (size_t)G->n, s, msg, "PageRank w");
   if (st == LAGR_OK) st = alloc_n(&pl->partials, (size_t)pl->np, s, msg, "partials");
-  if (st == LAGR_OK) st = alloc_n(&pl->hpart, (size_t)P->pr_at.nhc + 1, s, msg, "heavy chunk sums");
+  if (st == LAGR_OK) st = alloc_n(&pl->hpart, (size_t)P->pr_fwd.nhc + 1, s, msg, "heavy chunk sums");
   if (st == LAGR_OK) st = alloc_n(&pl->st, 1, s, msg, "PageRank state");
   if (st < 0) {
     pr_plan_destroy(pl, s);
@@ -582,10 +667,10 @@ static int pr_forward(float *rank, int32_t *iters, double *resid, lagr_graph G, 
                       int32_t itermax, const float *teleport, int32_t flags, const float *sc, PrState *st,
                       cudaStream_t s, char *msg) {
   LAGR_TRY(lagr_property_AT(G, s, msg));
-  LAGR_TRY(row_plan(&P->pr_at, G->at_rowptr, G->n, s, msg));
+  LAGR_TRY(row_plan(&P->pr_fwd, G->at_rowptr, G->n, s, msg, PR_WUNITS, PR_WHEAVY, PR_WHCHUNK));
   const int mode = (flags & LAGR_PR_WEIGHTED) ? 1 : 0;
   const float *warm = (flags & LAGR_PR_WARM_START) ? rank : nullptr;
-  return pr_solve(mode, G, P, P->pr_at, G->at_rowptr, G->at_colidx, G->at_val, rank, sc, teleport, nullptr, warm,
+  return pr_solve(mode, G, P, P->pr_fwd, G->at_rowptr, G->at_colidx, G->at_val, rank, sc, teleport, nullptr, warm,
                   damping, tol, itermax, (flags & LAGR_PR_DANGLING) ? 1 : 0, st, iters, resid, s, msg);
 }
 
@@ -666,10 +751,11 @@ extern "C" int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t
     r = rfwd.p;
   }
   LAGR_TRY(row_plan(&P->pr_a, G->rowptr, G->n, s, msg));
+  LAGR_TRY(row_plan(&P->pr_adj, G->rowptr, G->n, s, msg, PR_WUNITS, PR_WHEAVY, PR_WHCHUNK));
   int32_t k = 0;
   double resid = 0.0;
-  LAGR_TRY(pr_solve(2, G, P, P->pr_a, G->rowptr, G->colidx, G->val, lam.p, sc.p, teleport, dL_drank, nullptr, damping,
-                    tol, itermax, dangling, st.p, &k, &resid, s, msg));
+  LAGR_TRY(pr_solve(2, G, P, P->pr_adj, G->rowptr, G->colidx, G->val, lam.p, sc.p, teleport, dL_drank, nullptr,
+                    damping, tol, itermax, dangling, st.p, &k, &resid, s, msg));
   if (dL_dw && G->nnz > 0) {
     // every row, heavy ones included, lies in some block's contiguous entry range
     pr_edge_grad<<<P->pr_a.nblk, PR_THREADS, 0, s>>>(G->rowptr, G->colidx, P->pr_a.blk, r, lam.p, damping, dL_dw);
@@ -683,7 +769,8 @@ extern "C" int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t
     LAGR_TRY(scratch.alloc(G->n, msg, "scratch"));
     pr_init<1><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(G->n, scratch.p, nullptr, sc.p, r, teleport, 1.0f / (float)G->n,
                                                    partials.p);
-    pr_finalize<<<1, 1024, 0, s>>>(partials.p, PR_INIT_BLOCKS, st.p, 1, damping, dangling, 0.0, 1, 1);
+    pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials.p, PR_INIT_BLOCKS, st.p, 1, damping, dangling, 0.0,
+                                                         1, 1);
     pr_teleport_grad<<<grid_for(G->n, 256), 256, 0, s>>>(G->n, lam.p, st.p, damping, dangling, dL_dteleport);
     LAGR_LAUNCH_CHECK();
   }

@@ -202,21 +202,23 @@ __global__ void gather_transpose(const int32_t *__restrict__ perm, const int32_t
 
 // ---- row plan -----------------------------------------------------------------------------------
 
-__global__ void light_degree(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ ld) {
+__global__ void light_degree(const int32_t *__restrict__ rowptr, int32_t n, int32_t heavy,
+                             int32_t *__restrict__ ld) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t d = rowptr[i + 1] - rowptr[i];
-    ld[i] = d <= ROW_HEAVY ? d : 0;
+    ld[i] = d <= heavy ? d : 0;
   }
 }
 
-// blk[b] = first row r with lp[r] + r >= b * ROW_UNITS (lp = exclusive prefix of light degrees)
-__global__ void block_starts(const int32_t *__restrict__ lp, int32_t n, int32_t nblk, int32_t *__restrict__ blk) {
+// blk[b] = first row r with lp[r] + r >= b * units (lp = exclusive prefix of light degrees)
+__global__ void block_starts(const int32_t *__restrict__ lp, int32_t n, int32_t nblk, int32_t units,
+                             int32_t *__restrict__ blk) {
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nblk; b += (int64_t)gridDim.x * blockDim.x) {
     if (b == nblk) {
       blk[b] = n;
       continue;
     }
-    const int64_t target = b * (int64_t)ROW_UNITS;
+    const int64_t target = b * (int64_t)units;
     int32_t lo = 0, hi = n;  // answer in [lo, hi]
     while (lo < hi) {
       const int32_t mid = lo + ((hi - lo) >> 1);
@@ -227,10 +229,10 @@ __global__ void block_starts(const int32_t *__restrict__ lp, int32_t n, int32_t 
 }
 
 __global__ void heavy_chunk_counts(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ heavy, int32_t nh,
-                                   int32_t *__restrict__ nch) {
+                                   int32_t hchunk, int32_t *__restrict__ nch) {
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
     const int32_t d = rowptr[heavy[h] + 1] - rowptr[heavy[h]];
-    nch[h] = (d + ROW_HCHUNK - 1) / ROW_HCHUNK;
+    nch[h] = (d + hchunk - 1) / hchunk;
   }
 }
 
@@ -353,10 +355,11 @@ int transpose_csr(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *
 }
 
 // Build (once) the row plan of a CSR: heavy rows and row blocks.  Synchronises the stream.
-int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg) {
+int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg, int32_t units, int32_t hv,
+             int32_t hchunk) {
   if (pl->nblk >= 0) return LAGR_OK;
   int32_t *heavy = nullptr, nheavy = 0;
-  LAGR_TRY(heavy_rows(rowptr, n, ROW_HEAVY, &heavy, &nheavy, s, msg));
+  LAGR_TRY(heavy_rows(rowptr, n, hv, &heavy, &nheavy, s, msg));
   Temp<int32_t> ld(s), lp(s);
   int st = ld.alloc(n, msg, "light degrees");
   if (st == LAGR_OK) st = lp.alloc((size_t)n + 1, msg, "light prefix");
@@ -364,7 +367,7 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
     dev_free(heavy, s);
     return st;
   }
-  light_degree<<<grid_for(n, 256), 256, 0, s>>>(rowptr, n, ld.p);
+  light_degree<<<grid_for(n, 256), 256, 0, s>>>(rowptr, n, hv, ld.p);
   st = exclusive_scan(ld.p, lp.p, n, s, msg);
   int32_t light = 0;
   cudaError_t e = cudaGetLastError();
@@ -376,7 +379,7 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
   }
   // block starts: the first row at or after every ROW_UNITS-th unit, plus each heavy row and the
   // row after it, so that every heavy row is a block of its own (merged on the host, once)
-  const int64_t nb0 = ((int64_t)light + n) / ROW_UNITS + 1;
+  const int64_t nb0 = ((int64_t)light + n) / units + 1;
   int32_t *blk = nullptr;
   uint8_t *hblk = nullptr;
   int64_t nblk = 0;
@@ -384,7 +387,7 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
     Temp<int32_t> b0(s);
     if (st == LAGR_OK) st = b0.alloc((size_t)nb0 + 1, msg, "row block starts");
     if (st == LAGR_OK) {
-      block_starts<<<grid_for(nb0 + 1, 256), 256, 0, s>>>(lp.p, n, (int32_t)nb0, b0.p);
+      block_starts<<<grid_for(nb0 + 1, 256), 256, 0, s>>>(lp.p, n, (int32_t)nb0, units, b0.p);
       e = cudaGetLastError();
     }
     std::vector<int32_t> hb((size_t)nb0 + 1), hh((size_t)nheavy);
@@ -444,7 +447,7 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
     st = nch.alloc(nheavy, msg, "heavy chunk counts");
     if (st == LAGR_OK) st = alloc_n(&hc_off, (size_t)nheavy + 1, s, msg, "heavy chunk offsets");
     if (st == LAGR_OK) {
-      heavy_chunk_counts<<<grid_for(nheavy, 256), 256, 0, s>>>(rowptr, heavy, nheavy, nch.p);
+      heavy_chunk_counts<<<grid_for(nheavy, 256), 256, 0, s>>>(rowptr, heavy, nheavy, hchunk, nch.p);
       st = exclusive_scan(nch.p, hc_off, nheavy, s, msg);
     }
     if (st == LAGR_OK) {
@@ -481,6 +484,9 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
   pl->hc_row = hc_row;
   pl->nhc = nhc;
   pl->hblk = hblk;
+  pl->units = units;
+  pl->heavy_len = hv;
+  pl->hchunk = hchunk;
   return LAGR_OK;
 }
 

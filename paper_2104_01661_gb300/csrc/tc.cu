@@ -28,13 +28,16 @@ constexpr int TCW_WARPS = 8;          // warps per CTA in the warp-anchor kernel
 constexpr int TCW_SLOTS = 512;        // hash slots per warp (entries below the window)
 constexpr int TCW_MAXD = TCW_SLOTS / 2;  // warp anchors: d+ <= wmax <= 256 ...
 constexpr int TCW_MAXDEG = 4096;      // ... and degree <= 4096
-constexpr int TCW_CHUNK = 256;       // warp anchors with more neighbours are cut into items of this many
-constexpr int TCW_GRAB = 8;          // short warp anchors taken per queue atomic
+constexpr int TCW_HEAVY = 8192;      // warp anchors with deg * d+ above this are queued first
+constexpr int TCW_ITEMWORK = 65536;  // ... and above this cut into items of TCW_CHUNK neighbours
+constexpr int TCW_CHUNK = 256;
+constexpr int TCW_GRAB = 8;          // whole-anchor warp items taken per queue atomic
 constexpr int TCW_WIN_LOG = 15;       // per-warp window: the top 32768 ranks (4 KB of bits)
 constexpr int TCC_THREADS = 512;      // CTA-anchor kernel
 constexpr int TCC_SLOTS = 8192;       // hash slots per CTA (32 KB)
 constexpr int TCC_WIN_LOG = 17;       // per-CTA window: the top 131072 ranks (16 KB of bits)
 constexpr int TCC_CHUNK = 2048;       // default neighbours per CTA work item
+constexpr int TCC_MAXCHUNK = 4096;    // most neighbours per CTA work item
 constexpr int32_t EMPTY = -1;
 constexpr size_t TCW_SMEM = (size_t)TCW_WARPS * (((1 << TCW_WIN_LOG) / 32) * 4 + TCW_SLOTS * 4);
 constexpr size_t TCC_SMEM = ((1 << TCC_WIN_LOG) / 32) * 4 + TCC_SLOTS * 4;
@@ -44,11 +47,12 @@ constexpr int SL_SORT = SC_COUNT0;
 constexpr int SL_DECIDE = SC_COUNT1;
 constexpr int SL_NW = SC_COUNT2;
 constexpr int SL_NC = SC_COUNT3;
-constexpr int SL_NWL = SC_COUNT4;  // warp anchors with at most TCW_CHUNK neighbours (one item each)
+constexpr int SL_NWL = SC_COUNT4;  // light warp anchors (one item each), stored from the end of listw
 constexpr int SL_QW = SC_COUNT5;   // queue cursor of the chunked warp items (SL_NW of them)
 constexpr int SL_QC = SC_COUNT6;
 constexpr int SL_TOTAL = SC_COUNT7;
-constexpr int SL_QWL = SC_COUNT8;  // queue cursor of the short warp anchors
+constexpr int SL_QWL = SC_COUNT8;  // queue cursor of the whole-anchor warp items
+constexpr int SL_NWF = SC_COUNT9;  // heavier warp anchors (one item each), stored from the front of listw
 
 __device__ __forceinline__ uint32_t hslot(int32_t w, int logT) {
   return ((uint32_t)w * 0x9E3779B1u) >> (32 - logT);
@@ -325,15 +329,22 @@ __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *_
     const bool active = a > 0;
     const bool is_w = active && a <= wmax && dg <= TCW_MAXDEG;
     const int nch = (active && !is_w) ? (dg + chunk - 1) / chunk : 0;
-    // warp-class anchors: one item each when they have at most TCW_CHUNK neighbours, else one
-    // item per TCW_CHUNK neighbours (so that no warp item is much longer than the others)
-    const bool wl = is_w && dg <= TCW_CHUNK;
-    const unsigned bl = __ballot_sync(LAGR_FULL_MASK, wl);
-    unsigned long long pl = 0;
+    // warp-class anchors: the few whose deg * d+ exceeds TCW_ITEMWORK are cut into items of
+    // TCW_CHUNK neighbours (no warp item much longer than the others); the rest are one item each,
+    // the heavier ones (deg * d+ above TCW_HEAVY) from the front of listw, the others from its
+    // end, so that the warps take the long items first and the short ones last
+    const int64_t work = (int64_t)dg * a;
+    const bool wi = is_w && work > TCW_ITEMWORK;
+    const bool wf = is_w && !wi && work > TCW_HEAVY, wl = is_w && !wi && !wf;
+    const unsigned bf = __ballot_sync(LAGR_FULL_MASK, wf), bl = __ballot_sync(LAGR_FULL_MASK, wl);
+    unsigned long long pf = 0, pl = 0;
+    if (lane == 0 && bf) pf = atomicAdd((unsigned long long *)&dscal[SL_NWF], (unsigned long long)__popc(bf));
     if (lane == 0 && bl) pl = atomicAdd((unsigned long long *)&dscal[SL_NWL], (unsigned long long)__popc(bl));
+    pf = __shfl_sync(LAGR_FULL_MASK, pf, 0);
     pl = __shfl_sync(LAGR_FULL_MASK, pl, 0);
-    if (wl) listw[pl + __popc(bl & lt)] = (int32_t)v;
-    const int nwi = (is_w && !wl) ? (dg + TCW_CHUNK - 1) / TCW_CHUNK : 0;
+    if (wf) listw[pf + __popc(bf & lt)] = (int32_t)v;
+    if (wl) listw[(int64_t)n - 1 - (int64_t)(pl + __popc(bl & lt))] = (int32_t)v;
+    const int nwi = wi ? (dg + TCW_CHUNK - 1) / TCW_CHUNK : 0;
     const int winc = warp_inclusive_scan(nwi);
     const int wtot = __shfl_sync(LAGR_FULL_MASK, winc, 31);
     unsigned long long pw = 0;
@@ -419,7 +430,7 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
     tc_count_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                   const int32_t *__restrict__ u_rowptr, const int32_t *__restrict__ u_colidx,
                   const int32_t *__restrict__ dplus, const int32_t *__restrict__ rank,
-                  const int32_t *__restrict__ listw, const int2 *__restrict__ listwh, int64_t capwh,
+                  const int32_t *__restrict__ listw, int32_t n, const int2 *__restrict__ listwh, int64_t capwh,
                   int64_t *__restrict__ dscal, int32_t w0,
                   const int32_t *__restrict__ voff, int32_t ngraphs, unsigned long long *__restrict__ counts) {
   extern __shared__ uint32_t wsm[];  // per warp: window bits, then hash slots
@@ -430,13 +441,44 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
   int32_t *tab = reinterpret_cast<int32_t *>(bm + WORDS);
   for (int i = lane; i < WORDS; i += 32) bm[i] = 0u;
   __syncwarp();
-  const int64_t nwh = min(dscal[SL_NW], capwh), nwl = dscal[SL_NWL];
+  const int64_t nwh = min(dscal[SL_NW], capwh), nwf = dscal[SL_NWF], nwl = nwf + dscal[SL_NWL];
   unsigned long long mine = 0;
-  // one warp item: the anchor x's neighbours [jb0, je) against x's set
-  auto item = [&](int32_t x, int32_t jb0, int32_t je) {
+  // Work items: first the chunks of the long anchors (one per queue atomic), then whole anchors,
+  // TCW_GRAB per queue atomic (most are tiny: one atomic each would serialise the warps on the
+  // counter), the heavier ones from the front of listw first.
+  bool chunks = true;
+  long long it = 0, it_end = 0;
+  for (;;) {
+    int32_t x, jb0, je;
+    if (chunks) {
+      long long c = 0;
+      if (lane == 0) c = (long long)atomicAdd((unsigned long long *)&dscal[SL_QW], 1ull);
+      c = __shfl_sync(LAGR_FULL_MASK, c, 0);
+      if (c < nwh) {
+        const int2 w = listwh[c];
+        x = w.x;
+        jb0 = rowptr[x] + w.y;
+        je = min(rowptr[x + 1], jb0 + TCW_CHUNK);
+      } else {
+        chunks = false;
+      }
+    }
+    if (!chunks) {
+      if (it == it_end) {
+        if (lane == 0) it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QWL], (unsigned long long)TCW_GRAB);
+        it = __shfl_sync(LAGR_FULL_MASK, it, 0);
+        it_end = min(it + TCW_GRAB, (long long)nwl);
+      }
+      if (it >= nwl) break;
+      x = it < nwf ? listw[it] : listw[n - 1 - (it - nwf)];
+      jb0 = rowptr[x];
+      je = rowptr[x + 1];
+      it++;
+    }
+    // the anchor x's neighbours [jb0, je) against x's set (the table is cleared for every item,
+    // so it is valid whether or not entries fall below w0)
     const int32_t a = dplus[x];
     const int32_t ub = u_rowptr[x];
-    // the table is cleared for every item, so it is valid whether or not entries fall below w0
     const RankSet rs{bm, tab, ceil_log2(2 * a), w0, rank[x], nullptr, 0, false, true};
     const int T = 1 << rs.logT;
     for (int i = lane; i < T; i += 32) tab[i] = EMPTY;
@@ -455,29 +497,6 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
       mine += c;
     }
     __syncwarp();
-  };
-  // first the chunked items of the long anchors, one per queue atomic
-  for (;;) {
-    long long it = 0;
-    if (lane == 0) it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QW], 1ull);
-    it = __shfl_sync(LAGR_FULL_MASK, it, 0);
-    if (it >= nwh) break;
-    const int2 w = listwh[it];
-    const int32_t jb0 = rowptr[w.x] + w.y;
-    item(w.x, jb0, min(rowptr[w.x + 1], jb0 + TCW_CHUNK));
-  }
-  // then the short anchors, TCW_GRAB per queue atomic (most of them are tiny: one atomic each
-  // would serialise the warps on the counter)
-  for (;;) {
-    long long it = 0;
-    if (lane == 0) it = (long long)atomicAdd((unsigned long long *)&dscal[SL_QWL], (unsigned long long)TCW_GRAB);
-    it = __shfl_sync(LAGR_FULL_MASK, it, 0);
-    if (it >= nwl) break;
-    const long long it_end = min(it + TCW_GRAB, (long long)nwl);
-    for (; it < it_end; it++) {
-      const int32_t x = listw[it];
-      item(x, rowptr[x], rowptr[x + 1]);
-    }
   }
   if (!voff) {
     mine = block_sum(mine, red);
@@ -575,7 +594,7 @@ TcParams tc_default_params() { return TcParams{TCC_CHUNK, TCW_MAXD}; }
 int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
   const int32_t n = G->n;
   const int64_t nnz = G->nnz;
-  if (prm.wmax < 1 || prm.wmax > TCW_MAXD || prm.chunk < 32) {
+  if (prm.wmax < 1 || prm.wmax > TCW_MAXD || prm.chunk < 32 || prm.chunk > TCC_MAXCHUNK) {
     set_msg(msg, "bad triangle-count partition (wmax=%d, chunk=%d)", prm.wmax, prm.chunk);
     return LAGR_ERR_INVALID_VALUE;
   }
@@ -683,7 +702,7 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
   {
     KTimer kt(TK_TC_WARP, s);
     tc_count_warp<<<152 * 4, TCW_WARPS * 32, TCW_SMEM, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx,
-                                                            P->tc_dplus, P->tc_rank, P->tc_listw, P->tc_listwh,
+                                                            P->tc_dplus, P->tc_rank, P->tc_listw, n, P->tc_listwh,
                                                             P->tc_capwh, P->dscal, w0w,
                                                             voff, ngraphs, counts);
   }
