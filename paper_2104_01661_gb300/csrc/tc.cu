@@ -99,8 +99,10 @@ struct RankSet {
   }
   __device__ __forceinline__ uint32_t has(int32_t w) const {
     const int32_t d = w - w0;
-    // in the window the bitmap decides alone (it holds no rank <= rx)
-    if (d >= 0) return (bm[d >> 5] >> (d & 31)) & 1u;
+    // in the window the bitmap decides alone (it holds no rank <= rx); the word is read with a
+    // clamped index so that the common case has no branch
+    const uint32_t in = (bm[max(d, 0) >> 5] >> (d & 31)) & 1u;
+    if (d >= 0) return in;
     if (w <= rx || !below) return 0;  // the anchor's entries all rank above it
     if (!scan) return (uint32_t)hprobe(tab, logT, w);
     for (int32_t q = 0; q < len; q++)
@@ -414,14 +416,14 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
   while (longs) {
     const int sl = __ffs(longs) - 1;
     longs &= longs - 1;
-    const int32_t st_s = __shfl_sync(LAGR_FULL_MASK, st, sl);
+    const int32_t *lst = u_colidx + __shfl_sync(LAGR_FULL_MASK, st, sl);
     const int32_t len_s = __shfl_sync(LAGR_FULL_MASK, len, sl);
     int32_t k = lane;
-    for (; k + 32 < len_s; k += 64) {
-      const int32_t w0 = u_colidx[st_s + k], w1 = u_colidx[st_s + k + 32];
-      c += probe(w0) + probe(w1);
+    for (; k + 96 < len_s; k += 128) {  // four loads per lane in flight
+      const int32_t w0 = lst[k], w1 = lst[k + 32], w2 = lst[k + 64], w3 = lst[k + 96];
+      c += (probe(w0) + probe(w1)) + (probe(w2) + probe(w3));
     }
-    if (k < len_s) c += probe(u_colidx[st_s + k]);
+    for (; k < len_s; k += 32) c += probe(lst[k]);
   }
   return c;
 }
