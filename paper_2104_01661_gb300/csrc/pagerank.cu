@@ -31,7 +31,7 @@ namespace {
 
 constexpr int PR_THREADS = 256;
 constexpr int PR_UNITS = ROW_UNITS;                 // units (entries + rows) per edge-gradient block
-constexpr int PR_WUNITS = 960;    // units per block of the gathers' row plans (one warp's work item)
+constexpr int PR_WUNITS = 1024;   // units per block of the gathers' row plans (one warp's work item)
 constexpr int PR_WHEAVY = 1024;   // longer rows are cut into chunks of PR_WHCHUNK entries
 constexpr int PR_WHCHUNK = 2048;
 constexpr int PR_CHUNK = 8;                         // iterations launched between host checks
@@ -185,19 +185,14 @@ __device__ __forceinline__ int32_t srow_of(const int32_t *rp, int32_t lo, int32_
 }
 
 // one row block (at most PR_WUNITS units), one warp: writes the block's partials.  srp: this
-// warp's shared-memory copy of the block's row pointers; crow / csum: this warp's PR_EPL slots per
-// lane where a lane lists the rows it closes in a step, so that the row outputs then run in as
-// many lane-parallel rounds as the busiest lane has rows (not one round per entry position).
+// warp's shared-memory copy of the block's row pointers.
 template <int MODE>
 __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const int32_t *__restrict__ blk,
                                            const uint8_t *__restrict__ hblk, int32_t wb,
-                                           double2 *__restrict__ partials, int32_t *srp, int16_t *crow,
-                                           float *csum) {
+                                           double2 *__restrict__ partials, int32_t *srp) {
   const int lane = threadIdx.x & 31;
   const int32_t r0 = blk[wb], r1 = blk[wb + 1];
   const int32_t nr = r1 - r0;
-  int16_t *myrow = crow + lane * PR_EPL;
-  float *mysum = csum + lane * PR_EPL;
   double resid = 0.0, aux = 0.0;
   if (!hblk[wb]) {  // (a block that is one heavy row is summed by the chunk items)
     for (int32_t q = lane; q <= nr; q += 32) srp[q] = __ldg(a.rowptr + r0 + q);
@@ -226,8 +221,8 @@ __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const 
       bool fresh = false;   // the scan restarts at this lane (nothing open flows through it)
       bool hclose = false;  // the lane closes a row that began before it (needs the joined prefix)
       float hsum = 0.0f;
-      int32_t hrow = 0, ncl = 0;  // ncl: rows listed in this lane's slots
-      int32_t qend = rc;          // the row holding this lane's last entry
+      int32_t hrow = 0;
+      int32_t qend = rc;  // the row holding this lane's last entry
       if (ks < ke) {
         int32_t q = srow_of(srp, rc, nr - 1, ks);
         int32_t rs = srp[q], re = srp[q + 1];
@@ -238,16 +233,14 @@ __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const 
         for (int j = 0; j < PR_EPL; j++) {
           const int32_t k = k0 + j;
           if (k < ks || k >= ke) continue;
-          while (k >= re) {  // the row ended before k: list it, step over empty rows
+          while (k >= re) {  // the row ended before k: close it, step over empty rows
             if (re > rs) {
               if (first && open_head) {
                 hclose = true;
                 hsum = acc;
                 hrow = q;
               } else {
-                myrow[ncl] = (int16_t)q;
-                mysum[ncl] = acc;
-                ncl++;
+                row_out<MODE>(a, r0 + q, acc, coef, resid, aux);
               }
             }
             first = false;
@@ -265,9 +258,7 @@ __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const 
             hsum = acc;
             hrow = q;
           } else {
-            myrow[ncl] = (int16_t)q;
-            mysum[ncl] = acc;
-            ncl++;
+            row_out<MODE>(a, r0 + q, acc, coef, resid, aux);
           }
           fresh = true;
         } else {
@@ -290,20 +281,8 @@ __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const 
       if (!sf) sv += carry;
       float before = __shfl_up_sync(LAGR_FULL_MASK, sv, 1);
       if (lane == 0) before = carry;
-      if (hclose) {  // the row a lane closes first comes first in its list
-        for (int t = ncl; t > 0; t--) {
-          myrow[t] = myrow[t - 1];
-          mysum[t] = mysum[t - 1];
-        }
-        myrow[0] = (int16_t)hrow;
-        mysum[0] = before + hsum;
-        ncl++;
-      }
+      if (hclose) row_out<MODE>(a, r0 + hrow, before + hsum, coef, resid, aux);
       carry = __shfl_sync(LAGR_FULL_MASK, sv, 31);
-      // the row outputs, one listed row per lane per round
-      const int rounds = __reduce_max_sync(LAGR_FULL_MASK, (unsigned)ncl);
-      for (int t = 0; t < rounds; t++)
-        if (t < ncl) row_out<MODE>(a, r0 + myrow[t], mysum[t], coef, resid, aux);
       // the next step starts inside the row that holds this step's last entry (found by the lane
       // that holds that entry)
       rc = __shfl_sync(LAGR_FULL_MASK, qend, (min(gs + PR_STEP, e1) - 1 - gs) / PR_EPL);
@@ -349,8 +328,6 @@ __global__ void __launch_bounds__(PR_THREADS, MODE == 0 ? 5 : 4)
             const int32_t *__restrict__ heavy, const int32_t *__restrict__ hc_off, const int32_t *__restrict__ hc_row,
             int32_t nhc, int32_t hchunk, PrState *__restrict__ st, double2 *__restrict__ partials) {
   __shared__ int32_t s_rp[PR_THREADS / 32][PR_WUNITS + 2];  // each warp's row pointers
-  __shared__ int16_t s_crow[PR_THREADS / 32][PR_STEP];       // each warp's closed-row slots
-  __shared__ float s_csum[PR_THREADS / 32][PR_STEP];
   if (st->done) return;  // uniform over the grid
   const float coef = st->coef;
   const int lane = threadIdx.x & 31;
@@ -362,8 +339,7 @@ __global__ void __launch_bounds__(PR_THREADS, MODE == 0 ? 5 : 4)
     q = __shfl_sync(LAGR_FULL_MASK, q, 0);
     if (q >= nitems) break;
     if (q < nhc) warp_chunk<MODE>(a, heavy, hc_off, hc_row, hchunk, q);
-    else warp_block<MODE>(a, coef, blk, hblk, q - nhc, partials, srp, s_crow[threadIdx.x >> 5],
-                          s_csum[threadIdx.x >> 5]);
+    else warp_block<MODE>(a, coef, blk, hblk, q - nhc, partials, srp);
   }
 }
 
