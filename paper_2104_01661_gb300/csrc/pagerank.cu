@@ -97,6 +97,7 @@ struct IterArgs {
   int dangling;
   float *hpart;       // partial sums of the heavy-row chunks
   int vec;            // colidx (and val) are 16-byte aligned: steps load them as vectors
+  float *acc;         // the row sums of the gather, turned into the outputs by pr_epilogue
 };
 
 template <int MODE>
@@ -106,9 +107,12 @@ __device__ __forceinline__ float gather_one(const IterArgs &a, int32_t k) {
   return __ldg(&a.val[k]) * __ldg(&a.x[j]);
 }
 
+// a row's output from its sum; resid / aux collect this thread's share in float (a thread's
+// few rows), the block reduction continues in double (GB300's float64 rate is a small fraction
+// of its float32 rate)
 template <int MODE>
-__device__ __forceinline__ void row_out(const IterArgs &a, int32_t i, float acc, float coef, double &resid,
-                                        double &aux) {
+__device__ __forceinline__ void row_out(const IterArgs &a, int32_t i, float acc, float coef, float &resid,
+                                        float &aux) {
   const float vi = a.vvec ? a.vvec[i] : a.vuni;
   const float s = a.sc[i];
   float r;
@@ -122,9 +126,9 @@ __device__ __forceinline__ void row_out(const IterArgs &a, int32_t i, float acc,
     if (a.dangling && s == 0.0f) r += coef;
   }
   a.out[i] = r;
-  resid += fabs((double)a.prev[i] - (double)r);
-  if (MODE == 2) aux += (double)vi * (double)r;
-  else if (s == 0.0f) aux += (double)r;
+  resid += fabsf(a.prev[i] - r);
+  if (MODE == 2) aux += vi * r;
+  else if (s == 0.0f) aux += r;
 }
 
 // ---- one warp per row block ----------------------------------------------------------------------
@@ -184,21 +188,19 @@ __device__ __forceinline__ int32_t srow_of(const int32_t *rp, int32_t lo, int32_
   return lo;
 }
 
-// one row block (at most PR_WUNITS units), one warp: writes the block's partials.  srp: this
-// warp's shared-memory copy of the block's row pointers.
+// one row block (at most PR_WUNITS units), one warp: writes the block's row sums to a.acc.  srp:
+// this warp's shared-memory copy of the block's row pointers.
 template <int MODE>
-__device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const int32_t *__restrict__ blk,
-                                           const uint8_t *__restrict__ hblk, int32_t wb,
-                                           double2 *__restrict__ partials, int32_t *srp) {
+__device__ __forceinline__ void warp_block(const IterArgs &a, const int32_t *__restrict__ blk,
+                                           const uint8_t *__restrict__ hblk, int32_t wb, int32_t *srp) {
   const int lane = threadIdx.x & 31;
   const int32_t r0 = blk[wb], r1 = blk[wb + 1];
   const int32_t nr = r1 - r0;
-  double resid = 0.0, aux = 0.0;
   if (!hblk[wb]) {  // (a block that is one heavy row is summed by the chunk items)
     for (int32_t q = lane; q <= nr; q += 32) srp[q] = __ldg(a.rowptr + r0 + q);
     __syncwarp();
     for (int32_t q = lane; q < nr; q += 32)  // empty rows
-      if (srp[q] == srp[q + 1]) row_out<MODE>(a, r0 + q, 0.0f, coef, resid, aux);
+      if (srp[q] == srp[q + 1]) a.acc[r0 + q] = 0.0f;
     const int32_t e0 = srp[0], e1 = srp[nr];
     const int32_t kb = e0 & ~3;  // steps start 16-byte aligned
     int32_t rc = 0;              // the block row holding the first entry of the current step
@@ -240,7 +242,7 @@ __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const 
                 hsum = acc;
                 hrow = q;
               } else {
-                row_out<MODE>(a, r0 + q, acc, coef, resid, aux);
+                a.acc[r0 + q] = acc;
               }
             }
             first = false;
@@ -258,7 +260,7 @@ __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const 
             hsum = acc;
             hrow = q;
           } else {
-            row_out<MODE>(a, r0 + q, acc, coef, resid, aux);
+            a.acc[r0 + q] = acc;
           }
           fresh = true;
         } else {
@@ -281,7 +283,7 @@ __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const 
       if (!sf) sv += carry;
       float before = __shfl_up_sync(LAGR_FULL_MASK, sv, 1);
       if (lane == 0) before = carry;
-      if (hclose) row_out<MODE>(a, r0 + hrow, before + hsum, coef, resid, aux);
+      if (hclose) a.acc[r0 + hrow] = before + hsum;
       carry = __shfl_sync(LAGR_FULL_MASK, sv, 31);
       // the next step starts inside the row that holds this step's last entry (found by the lane
       // that holds that entry)
@@ -289,9 +291,6 @@ __device__ __forceinline__ void warp_block(const IterArgs &a, float coef, const 
     }
     __syncwarp();  // srp is rewritten by the warp's next block
   }
-  resid = warp_sum(resid);
-  aux = warp_sum(aux);
-  if (lane == 0) partials[wb] = make_double2(resid, aux);
 }
 
 // one chunk of hchunk entries of a heavy row, one warp: its sum in hpart[cidx] (pr_heavy_finish
@@ -326,10 +325,9 @@ template <int MODE>
 __global__ void __launch_bounds__(PR_THREADS, MODE == 0 ? 5 : 4)
     pr_warp(IterArgs a, const int32_t *__restrict__ blk, int32_t nblk, const uint8_t *__restrict__ hblk,
             const int32_t *__restrict__ heavy, const int32_t *__restrict__ hc_off, const int32_t *__restrict__ hc_row,
-            int32_t nhc, int32_t hchunk, PrState *__restrict__ st, double2 *__restrict__ partials) {
+            int32_t nhc, int32_t hchunk, PrState *__restrict__ st) {
   __shared__ int32_t s_rp[PR_THREADS / 32][PR_WUNITS + 2];  // each warp's row pointers
   if (st->done) return;  // uniform over the grid
-  const float coef = st->coef;
   const int lane = threadIdx.x & 31;
   int32_t *srp = s_rp[threadIdx.x >> 5];
   const int32_t nitems = nhc + nblk;
@@ -339,32 +337,43 @@ __global__ void __launch_bounds__(PR_THREADS, MODE == 0 ? 5 : 4)
     q = __shfl_sync(LAGR_FULL_MASK, q, 0);
     if (q >= nitems) break;
     if (q < nhc) warp_chunk<MODE>(a, heavy, hc_off, hc_row, hchunk, q);
-    else warp_block<MODE>(a, coef, blk, hblk, q - nhc, partials, srp);
+    else warp_block<MODE>(a, blk, hblk, q - nhc, srp);
   }
 }
 
-// the heavy rows: add each row's chunk sums in chunk order, then the row's output
+// the heavy rows: add each row's chunk sums in chunk order
 constexpr int PR_HF_THREADS = 256;
-template <int MODE>
 __global__ void __launch_bounds__(PR_HF_THREADS)
     pr_heavy_finish(IterArgs a, const int32_t *__restrict__ heavy, int32_t nheavy, const int32_t *__restrict__ hc_off,
-                    const PrState *__restrict__ st, double2 *__restrict__ partials) {
-  __shared__ double red[32];
+                    const PrState *__restrict__ st) {
   if (st->done) return;
-  const float coef = st->coef;
-  double resid = 0.0, aux = 0.0;
   const int32_t h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h < nheavy) {
     float acc = 0.0f;
     for (int32_t c = hc_off[h]; c < hc_off[h + 1]; c++) acc += a.hpart[c];
-    row_out<MODE>(a, heavy[h], acc, coef, resid, aux);
+    a.acc[heavy[h]] = acc;
   }
-  resid = block_sum(resid, red);
-  aux = block_sum(aux, red);
+}
+
+// The element-wise rest of the iteration over the row sums: each row's output (the teleport or
+// adjoint term, the next gathered value, the residual and the dangling / v.lambda sum).  A fixed
+// grid of PR_EPI_BLOCKS CTAs, each with a fixed share of the rows, writes one partial pair per CTA
+// (deterministic).
+constexpr int PR_EPI_BLOCKS = 152 * 4;
+template <int MODE>
+__global__ void __launch_bounds__(PR_THREADS)
+    pr_epilogue(IterArgs a, int32_t n, const PrState *__restrict__ st, double2 *__restrict__ partials) {
+  __shared__ double red[32];
+  if (st->done) return;
+  const float coef = st->coef;
+  float fr = 0.0f, fa = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    row_out<MODE>(a, (int32_t)i, a.acc[i], coef, fr, fa);
+  const double resid = block_sum((double)fr, red);
+  const double aux = block_sum((double)fa, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(resid, aux);
 }
 
-// fold the partials in a fixed order; init != 0 only prepares the first coefficient
 // Fold the partials in a fixed order: CTA b sums the b-th contiguous share (a fixed tree), and the
 // CTA that arrives last adds the PR_FIN_BLOCKS sums in order and updates the state (the result does
 // not depend on which CTA is last).  init != 0 only prepares the first coefficient.
@@ -457,17 +466,15 @@ static inline int heavy_finish_blocks(const RowPlan &pl) {
   return (pl.nheavy + PR_HF_THREADS - 1) / PR_HF_THREADS;
 }
 
-static inline int n_partials(const RowPlan &pl) {
-  const int np = pl.nblk + heavy_finish_blocks(pl);
-  return np > PR_INIT_BLOCKS ? np : PR_INIT_BLOCKS;
-}
+static inline int n_partials() { return PR_EPI_BLOCKS > PR_INIT_BLOCKS ? PR_EPI_BLOCKS : PR_INIT_BLOCKS; }
 
 static inline int aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// one iteration: the row-block gather, the heavy rows, the fold of the partials
+// one iteration: the row-sum gather, the heavy rows' chunk sums, the element-wise epilogue and the
+// fold of its partials
 template <int MODE>
-static void launch_iter(const RowPlan &pl, const IterArgs &a, PrState *st, double2 *partials, int32_t itermax,
-                        double tol, cudaStream_t s) {
+static void launch_iter(const RowPlan &pl, const IterArgs &a, int32_t n, PrState *st, double2 *partials,
+                        int32_t itermax, double tol, cudaStream_t s) {
   // as many persistent CTAs as can be resident at once (no more than there are warp items)
   static int resident[3] = {0, 0, 0};
   if (resident[MODE] == 0) {
@@ -483,13 +490,12 @@ static void launch_iter(const RowPlan &pl, const IterArgs &a, PrState *st, doubl
   {
     KTimer kt(TK_PR_GATHER, s);
     pr_warp<MODE><<<grid, PR_THREADS, 0, s>>>(a, pl.blk, pl.nblk, pl.hblk, pl.heavy, pl.hc_off, pl.hc_row, pl.nhc,
-                                              pl.hchunk, st, partials);
+                                              pl.hchunk, st);
   }
   const int hfb = heavy_finish_blocks(pl);
-  if (hfb > 0)
-    pr_heavy_finish<MODE><<<hfb, PR_HF_THREADS, 0, s>>>(a, pl.heavy, pl.nheavy, pl.hc_off, st, partials + pl.nblk);
-  // fold exactly the slots written above (the rest may hold the init kernel's partials)
-  pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials, pl.nblk + hfb, st, MODE, a.damping, a.dangling, tol,
+  if (hfb > 0) pr_heavy_finish<<<hfb, PR_HF_THREADS, 0, s>>>(a, pl.heavy, pl.nheavy, pl.hc_off, st);
+  pr_epilogue<MODE><<<PR_EPI_BLOCKS, PR_THREADS, 0, s>>>(a, n, st, partials);
+  pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials, PR_EPI_BLOCKS, st, MODE, a.damping, a.dangling, tol,
                                                        itermax, 0);
 }
 
@@ -516,15 +522,16 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const in
                     char *msg) {
   const int32_t n = G->n;
   const int vec = aligned16(colidx) && (val == nullptr || aligned16(val));
-  Temp<float> buf1(s), w0(s), w1(s), hpart(s);
+  Temp<float> buf1(s), w0(s), w1(s), hpart(s), rsum(s);
   Temp<double2> partials(s);
   LAGR_TRY(buf1.alloc(n, msg, "PageRank work vector"));
+  LAGR_TRY(rsum.alloc(n, msg, "PageRank row sums"));
   LAGR_TRY(hpart.alloc((size_t)pl.nhc + 1, msg, "heavy chunk sums"));
   if (mode == 0) {
     LAGR_TRY(w0.alloc(n, msg, "PageRank w"));
     LAGR_TRY(w1.alloc(n, msg, "PageRank w"));
   }
-  const int np = n_partials(pl);
+  const int np = n_partials();
   LAGR_TRY(partials.alloc(np, msg, "PageRank partial sums"));
   LAGR_CUDA_TRY(cudaMemsetAsync(partials.p, 0, np * sizeof(double2), s));
   LAGR_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(PrState), s));
@@ -541,17 +548,17 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const in
     for (int c = 0; c < chunk; c++) {
       const int k = launched + c + 1;  // iteration number
       IterArgs a{rowptr, colidx, val, nullptr, x[(k - 1) & 1], x[k & 1], nullptr, sc, vvec, vuni, gvec, damping,
-                 dangling, hpart.p, vec};
+                 dangling, hpart.p, vec, rsum.p};
       if (mode == 0) {
         a.x = w[(k - 1) & 1];
         a.wout = w[k & 1];
-        launch_iter<0>(pl, a, st, partials.p, itermax, (double)tol, s);
+        launch_iter<0>(pl, a, n, st, partials.p, itermax, (double)tol, s);
       } else if (mode == 1) {
         a.x = x[(k - 1) & 1];
-        launch_iter<1>(pl, a, st, partials.p, itermax, (double)tol, s);
+        launch_iter<1>(pl, a, n, st, partials.p, itermax, (double)tol, s);
       } else {
         a.x = x[(k - 1) & 1];
-        launch_iter<2>(pl, a, st, partials.p, itermax, (double)tol, s);
+        launch_iter<2>(pl, a, n, st, partials.p, itermax, (double)tol, s);
       }
     }
     LAGR_LAUNCH_CHECK();
@@ -598,7 +605,7 @@ struct PrPlan {
   RowPlan rows;  // borrowed from the graph's private state
   const float *vvec = nullptr;
   float damping = 0.85f;
-  float *sc = nullptr, *x1 = nullptr, *w0 = nullptr, *w1 = nullptr, *hpart = nullptr;
+  float *sc = nullptr, *x1 = nullptr, *w0 = nullptr, *w1 = nullptr, *hpart = nullptr, *rsum = nullptr;
   double2 *partials = nullptr;
   int np = 0;
   PrState *st = nullptr;
@@ -616,13 +623,14 @@ int pr_plan_create(PrPlan **out, lagr_graph G, Priv *P, float damping, const flo
   pl->rows = P->pr_fwd;
   pl->vvec = vvec;
   pl->damping = damping;
-  pl->np = n_partials(P->pr_fwd);
+  pl->np = n_partials();
   int st = alloc_n(&pl->sc, (size_t)G->n, s, msg, "PageRank scale");
   if (st == LAGR_OK) st = alloc_n(&pl->x1, (size_t)G->n, s, msg, "PageRank work vector");
   if (st == LAGR_OK) st = alloc_n(&pl->w0, (size_t)G->n, s, msg, "PageRank w");
   if (st == LAGR_OK) st = alloc_n(&pl->w1, (size_t)G->n, s, msg, "PageRank w");
   if (st == LAGR_OK) st = alloc_n(&pl->partials, (size_t)pl->np, s, msg, "partials");
   if (st == LAGR_OK) st = alloc_n(&pl->hpart, (size_t)P->pr_fwd.nhc + 1, s, msg, "heavy chunk sums");
+  if (st == LAGR_OK) st = alloc_n(&pl->rsum, (size_t)G->n, s, msg, "PageRank row sums");
   if (st == LAGR_OK) st = alloc_n(&pl->st, 1, s, msg, "PageRank state");
   if (st < 0) {
     pr_plan_destroy(pl, s);
@@ -643,8 +651,8 @@ int pr_plan_enqueue(PrPlan *pl, float *out, const float *warm, int32_t iters, cu
   launch_init(0, pl->n, out, w[0], pl->sc, warm, pl->vvec, vuni, pl->st, pl->partials, pl->damping, 0, iters, 0.0, s);
   for (int k = 1; k <= iters; k++) {
     IterArgs a{pl->rowptr, pl->colidx, nullptr, w[(k - 1) & 1], x[(k - 1) & 1], x[k & 1], w[k & 1], pl->sc,
-               pl->vvec, vuni, nullptr, pl->damping, 0, pl->hpart, aligned16(pl->colidx)};
-    launch_iter<0>(pl->rows, a, pl->st, pl->partials, iters, 0.0, s);
+               pl->vvec, vuni, nullptr, pl->damping, 0, pl->hpart, aligned16(pl->colidx), pl->rsum};
+    launch_iter<0>(pl->rows, a, pl->n, pl->st, pl->partials, iters, 0.0, s);
   }
   LAGR_LAUNCH_CHECK();
   if (iters & 1)
@@ -660,6 +668,7 @@ void pr_plan_destroy(PrPlan *pl, cudaStream_t s) {
   dev_free(pl->w1, s);
   dev_free(pl->partials, s);
   dev_free(pl->hpart, s);
+  dev_free(pl->rsum, s);
   dev_free(pl->st, s);
   delete pl;
 }
