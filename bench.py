@@ -458,10 +458,12 @@ def roofline(g, ktime, steps, peak, peak_kind, comp):
     pr_ms, pr_n = ktime["pr_gather"]
     tc_ms = ktime["tc_count_cta"][0] + ktime["tc_count_warp"][0]
     tc_n = ktime["tc_count_cta"][1]
-    pr_bytes = 4 * (n + 1) + 4 * nnz + 20 * n
+    # the gather kernel of one iteration: rowptr, colidx, the compulsory read of the gathered vector
+    # and the row sums it writes (the element-wise epilogue is a separate, streaming kernel)
+    pr_bytes = 4 * (n + 1) + 4 * nnz + 8 * n
     cand = []
     if pr_n:
-        cand.append((pr_ms, "pr_gather (PageRank row-block gather, one iteration)", pr_bytes, pr_ms / pr_n,
+        cand.append((pr_ms, "pr_warp (PageRank row-sum gather, one iteration)", pr_bytes, pr_ms / pr_n,
                      "pr_gather_rmat22.json"))
         comp["pagerank_gather_gbs"] = round(pr_bytes / (pr_ms / pr_n) / 1e6, 1)
     if tc_n:

@@ -36,7 +36,7 @@ constexpr int TCW_WIN_LOG = 15;       // per-warp window: the top 32768 ranks (4
 constexpr int TCC_THREADS = 512;      // CTA-anchor kernel
 constexpr int TCC_SLOTS = 8192;       // hash slots per CTA (32 KB)
 constexpr int TCC_WIN_LOG = 17;       // per-CTA window: the top 131072 ranks (16 KB of bits)
-constexpr int TCC_CHUNK = 2048;       // default neighbours per CTA work item
+constexpr int TCC_CHUNK = 4096;       // default neighbours per CTA work item
 constexpr int TCC_MAXCHUNK = 4096;    // most neighbours per CTA work item
 constexpr int32_t EMPTY = -1;
 constexpr size_t TCW_SMEM = (size_t)TCW_WARPS * (((1 << TCW_WIN_LOG) / 32) * 4 + TCW_SLOTS * 4);
