@@ -404,15 +404,21 @@ __global__ void __launch_bounds__(BFS_THREADS)
       if (lane == 0) nbits[w] = 0;
       continue;
     }
-    int32_t par = -1;
+    int32_t par = -1, dv = 0;
     if (need) {
       const int32_t b = at_rowptr[v], e = at_rowptr[v + 1];
-      for (int32_t k = b; k < e; k++) {
+      dv = e - b;
+      // four in-neighbours per round, so that their column and frontier loads overlap
+      int32_t k = b;
+      for (; k + 3 < e && par < 0; k += 4) {
+        const int32_t u0 = at_colidx[k], u1 = at_colidx[k + 1], u2 = at_colidx[k + 2], u3 = at_colidx[k + 3];
+        const bool h0 = (fbits[u0 >> 5] >> (u0 & 31)) & 1u, h1 = (fbits[u1 >> 5] >> (u1 & 31)) & 1u;
+        const bool h2 = (fbits[u2 >> 5] >> (u2 & 31)) & 1u, h3 = (fbits[u3 >> 5] >> (u3 & 31)) & 1u;
+        par = h0 ? u0 : h1 ? u1 : h2 ? u2 : h3 ? u3 : -1;
+      }
+      for (; k < e && par < 0; k++) {
         const int32_t u = at_colidx[k];
-        if ((fbits[u >> 5] >> (u & 31)) & 1u) {
-          par = u;
-          break;
-        }
+        if ((fbits[u >> 5] >> (u & 31)) & 1u) par = u;
       }
     }
     const unsigned m = __ballot_sync(LAGR_FULL_MASK, par >= 0);
@@ -424,7 +430,8 @@ __global__ void __launch_bounds__(BFS_THREADS)
     if (par >= 0) {
       if (level) level[v] = lev;
       if (parent) parent[v] = par;
-      mdeg += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+      // the out-degree (the in-degree read above when A' is A)
+      mdeg += (unsigned long long)(at_rowptr == rowptr ? dv : rowptr[v + 1] - rowptr[v]);
     }
   }
   found_n = warp_sum(found_n);
