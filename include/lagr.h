@@ -108,13 +108,14 @@ typedef struct lagr_graph_struct {
   int32_t *row_degree;
 
   /* cached: triangle-counting orientation U (strict upper part after the
-   * optional degree ordering of Alg. 6), held by row: row v (original label)
-   * lists, in the order of A(v,:), the ranks of v's neighbours that rank
-   * above v, a rank being the position in the stable ascending-degree order
-   * (or the label itself when Alg. 6 does not sort).  u_order is the
+   * optional degree ordering of Alg. 6), held in the row slots of A: row v
+   * (original label) is u_colidx[rowptr[v] .. rowptr[v] + u_dplus[v]), the
+   * ranks of v's neighbours that rank above v in the order of A(v,:), a rank
+   * being the position in the stable ascending-degree order (or the label
+   * itself when Alg. 6 does not sort).  u_dplus: device [n+1] (d+ per vertex);
+   * u_colidx: device [nnz] (slots past a row's d+ are unused).  u_order is the
    * LAGR_TC_* method it was built for. */
-  int32_t *u_rowptr, *u_colidx;
-  int64_t u_nnz;
+  int32_t *u_dplus, *u_colidx;
   int32_t u_order;
 
   /* cached scalars */

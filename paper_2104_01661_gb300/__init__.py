@@ -68,9 +68,8 @@ class _GraphStruct(ctypes.Structure):
         ("at_val", ctypes.c_void_p),
         ("at_owned", ctypes.c_int32),
         ("row_degree", ctypes.c_void_p),
-        ("u_rowptr", ctypes.c_void_p),
+        ("u_dplus", ctypes.c_void_p),
         ("u_colidx", ctypes.c_void_p),
-        ("u_nnz", ctypes.c_int64),
         ("u_order", ctypes.c_int32),
         ("a_pattern_is_symmetric", ctypes.c_int32),
         ("ndiag", ctypes.c_int64),

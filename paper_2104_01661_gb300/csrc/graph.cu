@@ -83,11 +83,9 @@ int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out) {
 }
 
 static void free_tc_cache(Priv *P, cudaStream_t s) {
-  dev_free(P->tc_dplus, s);
   dev_free(P->tc_listw, s);
   dev_free(P->tc_listwh, s);
   dev_free(P->tc_listc, s);
-  dev_free(P->tc_scan, s);
   dev_free(P->tc_rank, s);
   dev_free(P->tc_sortbuf, s);
   dev_free(P->tc_radix, s);
@@ -96,8 +94,6 @@ static void free_tc_cache(Priv *P, cudaStream_t s) {
   P->tc_capwh = 0;
   P->tc_rank = P->tc_sortbuf = P->tc_radix = nullptr;
   P->tc_radix_scan = nullptr;
-  P->tc_scan = nullptr;
-  P->tc_dplus = nullptr;
   P->tc_listw = nullptr;
   P->tc_listc = nullptr;
   P->tc_capc = 0;
@@ -351,7 +347,6 @@ int lagr_graph_new(lagr_graph *G, int32_t n, int64_t nnz, const int32_t *rowptr,
   g->val = val;
   g->a_pattern_is_symmetric = (kind == LAGR_UNDIRECTED) ? 1 : -1;
   g->ndiag = -1;
-  g->u_nnz = -1;
   g->u_order = -1;
   g->last_levels = g->last_push_levels = g->last_pull_levels = g->last_iters = -1;
   g->last_resid = -1.0;
@@ -376,10 +371,9 @@ int lagr_delete_properties(lagr_graph G, void *stream, char *msg) {
   G->at_owned = 0;
   dev_free(G->row_degree, s);
   G->row_degree = nullptr;
-  dev_free(G->u_rowptr, s);
+  dev_free(G->u_dplus, s);
   dev_free(G->u_colidx, s);
-  G->u_rowptr = G->u_colidx = nullptr;
-  G->u_nnz = -1;
+  G->u_dplus = G->u_colidx = nullptr;
   G->u_order = -1;
   G->ndiag = -1;
   priv_release(G, s);

@@ -107,14 +107,12 @@ struct Priv {
   int64_t *dscal = nullptr;  // LAGR_NSCAL int64 slots
   int64_t *hscal = nullptr;  // pinned host mirror
   // triangle counting: anchors of the warp class and CTA-class items (x, first neighbour)
-  int32_t *tc_dplus = nullptr;
   int32_t *tc_listw = nullptr;
   int2 *tc_listc = nullptr;
   int32_t *tc_rank = nullptr;   // degree rank (the A(p,p) labels of Alg. 6) or the id
   int32_t *tc_sortbuf = nullptr;  // 4n keys/values/work for the rank sort
   int32_t *tc_radix = nullptr;  // radix scratch
   int64_t *tc_radix_scan = nullptr;
-  int64_t *tc_scan = nullptr;
   int64_t tc_capc = 0;
   int2 *tc_listwh = nullptr;  // warp items of the warp anchors with many neighbours
   int64_t tc_capwh = 0;

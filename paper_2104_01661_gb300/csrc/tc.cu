@@ -167,18 +167,16 @@ __global__ void tc_rank_scatter(const int32_t *__restrict__ vals, int32_t n, con
 
 // One CTA per row block (see RowPlan): the ranks of the block's neighbours are gathered into
 // shared memory with coalesced colidx loads, then each short row is oriented by one thread and
-// each longer row by one warp.  FILL = false counts d+(v); FILL = true writes U(v,:) (the ranks
-// above rank(v), in the order of A(v,:); ballots keep the order inside a warp).  Rows longer than
-// ROW_HEAVY are left to the heavy kernels.
+// each longer row by one warp, in one pass: U(v,:) (the ranks above rank(v), in the order of
+// A(v,:); ballots keep the order inside a warp) is written into the first slots of A's row v, and
+// its length d+(v) to dplus[v].  Rows longer than ROW_HEAVY are left to tc_orient_heavy.
 constexpr int OR_STAGE = ROW_UNITS + ROW_HEAVY + 64;
 constexpr int OR_SHORT = 32;
 
-template <bool FILL>
 __global__ void __launch_bounds__(256)
     tc_orient_rows(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                   const int32_t *__restrict__ rank, const int32_t *__restrict__ blk, int64_t *__restrict__ dscal,
-                   int32_t *__restrict__ dplus, const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx,
-                   int64_t ucap) {
+                   const int32_t *__restrict__ rank, const int32_t *__restrict__ blk, int32_t *__restrict__ dplus,
+                   int32_t *__restrict__ u_colidx) {
   __shared__ int32_t stage[OR_STAGE];
   __shared__ int32_t longrows[ROW_UNITS / (OR_SHORT + 1) + 2];
   __shared__ int n_long;
@@ -207,21 +205,12 @@ __global__ void __launch_bounds__(256)
     const int32_t b = rowptr[v], e = rowptr[v + 1], dv = e - b;
     if (dv <= OR_SHORT) {
       const int32_t rv = rank[v];
-      if (FILL) {
-        int64_t out = u_rowptr[v];
-        for (int32_t q = b; q < e; q++) {
-          const int32_t ru = ru_of(q);
-          if (ru > rv) {
-            if (out < ucap) u_colidx[out] = ru;
-            else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
-            out++;
-          }
-        }
-      } else {
-        int cnt = 0;
-        for (int32_t q = b; q < e; q++) cnt += ru_of(q) > rv;
-        dplus[v] = cnt;
+      int32_t out = b;
+      for (int32_t q = b; q < e; q++) {
+        const int32_t ru = ru_of(q);
+        if (ru > rv) u_colidx[out++] = ru;  // out < e: the slots of row v
       }
+      dplus[v] = out - b;
     } else if (dv <= ROW_HEAVY) {
       longrows[atomicAdd(&n_long, 1)] = v;
     }
@@ -231,8 +220,7 @@ __global__ void __launch_bounds__(256)
   for (int q = warp; q < n_long; q += 8) {
     const int32_t v = longrows[q];
     const int32_t b = rowptr[v], e = rowptr[v + 1], rv = rank[v];
-    int64_t out = FILL ? u_rowptr[v] : 0;
-    int cnt = 0;
+    int32_t out = b;
     for (int32_t base = b; base < e; base += 32) {
       const int32_t k = base + lane;
       int32_t ru = 0;
@@ -241,50 +229,25 @@ __global__ void __launch_bounds__(256)
         ru = ru_of(k);
         f = ru > rv;
       }
-      if (FILL) {
-        const unsigned bal = __ballot_sync(LAGR_FULL_MASK, f);
-        if (f) {
-          const int64_t pos = out + __popc(bal & lt);
-          if (pos < ucap) u_colidx[pos] = ru;
-          else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
-        }
-        out += __popc(bal);
-      } else {
-        cnt += f;
-      }
+      const unsigned bal = __ballot_sync(LAGR_FULL_MASK, f);
+      if (f) u_colidx[out + __popc(bal & lt)] = ru;
+      out += __popc(bal);
     }
-    if (!FILL) {
-      cnt = warp_sum(cnt);
-      if (lane == 0) dplus[v] = cnt;
-    }
+    if (lane == 0) dplus[v] = out - b;
   }
 }
 
-__global__ void tc_orient_count_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                      const int32_t *__restrict__ rank, int32_t *__restrict__ dplus,
-                                      const int32_t *__restrict__ heavy, int32_t nh) {
-  __shared__ int red[32];
-  for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
-    const int32_t v = heavy[h];
-    const int32_t b = rowptr[v], e = rowptr[v + 1], rv = rank[v];
-    int cnt = 0;
-    for (int32_t k = b + threadIdx.x; k < e; k += blockDim.x) cnt += __ldg(&rank[colidx[k]]) > rv;
-    cnt = block_sum(cnt, red);
-    if (threadIdx.x == 0) dplus[v] = cnt;
-  }
-}
-
-__global__ void tc_orient_fill_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                     const int32_t *__restrict__ rank, int64_t *__restrict__ dscal,
-                                     const int32_t *__restrict__ u_rowptr, int32_t *__restrict__ u_colidx,
-                                     int64_t ucap, const int32_t *__restrict__ heavy, int32_t nh) {
+// the rows longer than ROW_HEAVY: one CTA each, the same output as tc_orient_rows
+__global__ void tc_orient_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                const int32_t *__restrict__ rank, int32_t *__restrict__ dplus,
+                                int32_t *__restrict__ u_colidx, const int32_t *__restrict__ heavy, int32_t nh) {
   __shared__ int wc[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const unsigned lt = lanemask_lt();
   for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
     const int32_t v = heavy[h];
     const int32_t b = rowptr[v], e = rowptr[v + 1], rv = rank[v];
-    int64_t out = u_rowptr[v];
+    int32_t out = b;
     for (int32_t base = b; base < e; base += blockDim.x) {
       const int32_t k = base + threadIdx.x;
       int32_t u = 0;
@@ -301,14 +264,11 @@ __global__ void tc_orient_fill_heavy(const int32_t *__restrict__ rowptr, const i
         if (w < warp) before += wc[w];
         total += wc[w];
       }
-      if (f) {
-        const int64_t pos = out + before + __popc(bal & lt);
-        if (pos < ucap) u_colidx[pos] = u;
-        else dscal[SC_ERR] = LAGR_ERR_INVALID_GRAPH;
-      }
+      if (f) u_colidx[out + before + __popc(bal & lt)] = u;
       __syncthreads();
       out += total;
     }
+    if (threadIdx.x == 0) dplus[v] = out - b;
   }
 }
 
@@ -374,11 +334,12 @@ __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *_
 // ---- intersection counts --------------------------------------------------------------------------
 
 // One batch of (up to) 32 neighbours A(x, jb..min(jb+32,e)): for every neighbour y anchored at x
-// (smaller (d+, id)), probe each element of U(y,:) against x's set.  Warp-collective.
+// (smaller (d+, id)), probe each element of U(y,:) = u_colidx[ustart[y] .. ustart[y] + dplus[y])
+// against x's set.  Warp-collective.
 template <class Probe>
 __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a, int32_t jb, int32_t e,
                                                            const int32_t *__restrict__ colidx,
-                                                           const int32_t *__restrict__ u_rowptr,
+                                                           const int32_t *__restrict__ ustart,
                                                            const int32_t *__restrict__ u_colidx,
                                                            const int32_t *__restrict__ dplus, Probe &&probe) {
   const int lane = threadIdx.x & 31;
@@ -389,7 +350,7 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
     const int32_t y = colidx[j];
     const int32_t dy = dplus[y];
     if (dy > 0 && (dy < a || (dy == a && y < x))) {
-      st = u_rowptr[y];
+      st = ustart[y];
       len = dy;
     }
   }
@@ -430,7 +391,7 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
 
 __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
     tc_count_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                  const int32_t *__restrict__ u_rowptr, const int32_t *__restrict__ u_colidx,
+                  const int32_t *__restrict__ ustart, const int32_t *__restrict__ u_colidx,
                   const int32_t *__restrict__ dplus, const int32_t *__restrict__ rank,
                   const int32_t *__restrict__ listw, int32_t n, const int2 *__restrict__ listwh, int64_t capwh,
                   int64_t *__restrict__ dscal, int32_t w0,
@@ -480,7 +441,7 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
     // the anchor x's neighbours [jb0, je) against x's set (the table is cleared for every item,
     // so it is valid whether or not entries fall below w0)
     const int32_t a = dplus[x];
-    const int32_t ub = u_rowptr[x];
+    const int32_t ub = ustart[x];
     const RankSet rs{bm, tab, ceil_log2(2 * a), w0, rank[x], nullptr, 0, false, true};
     const int T = 1 << rs.logT;
     for (int i = lane; i < T; i += 32) tab[i] = EMPTY;
@@ -489,7 +450,7 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
     __syncwarp();
     unsigned long long c = 0;
     for (int32_t jb = jb0; jb < je; jb += 32)
-      c += anchor_batch(x, a, jb, je, colidx, u_rowptr, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
+      c += anchor_batch(x, a, jb, je, colidx, ustart, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
     __syncwarp();
     for (int i = lane; i < a; i += 32) rs.erase(u_colidx[ub + i]);
     if (voff) {
@@ -508,7 +469,7 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
 
 __global__ void __launch_bounds__(TCC_THREADS)
     tc_count_cta(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                 const int32_t *__restrict__ u_rowptr, const int32_t *__restrict__ u_colidx,
+                 const int32_t *__restrict__ ustart, const int32_t *__restrict__ u_colidx,
                  const int32_t *__restrict__ dplus, const int32_t *__restrict__ rank, const int2 *__restrict__ listc,
                  int64_t *__restrict__ dscal, int32_t w0, const int32_t *__restrict__ voff, int32_t ngraphs,
                  unsigned long long *__restrict__ counts, int chunk, int64_t capc) {
@@ -536,7 +497,7 @@ __global__ void __launch_bounds__(TCC_THREADS)
     const int2 item = listc[it];
     const int32_t x = item.x;
     const int32_t a = dplus[x];
-    const int32_t ub = u_rowptr[x];
+    const int32_t ub = ustart[x];
     // how many entries fall below the window decides between the hash table and a scan
     int below = 0;
     for (int i = threadIdx.x; i < a; i += blockDim.x) below += u_colidx[ub + i] < w0;
@@ -562,7 +523,7 @@ __global__ void __launch_bounds__(TCC_THREADS)
       if (lane == 0) jb = atomicAdd(&s_next, 32);
       jb = __shfl_sync(LAGR_FULL_MASK, jb, 0);
       if (jb >= e) break;
-      c += anchor_batch(x, a, jb, e, colidx, u_rowptr, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
+      c += anchor_batch(x, a, jb, e, colidx, ustart, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
     }
     if (voff) {
       c = warp_sum(c);
@@ -601,22 +562,19 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
     return LAGR_ERR_INVALID_VALUE;
   }
   const int64_t capc = 2 * (nnz / (prm.wmax + 1) + nnz / (TCW_MAXDEG + 1)) + nnz / prm.chunk + 64;
-  if (G->u_rowptr && P->tc_listw && P->tc_capc >= capc) return LAGR_OK;
-  dev_free(G->u_rowptr, s);
+  if (G->u_colidx && P->tc_listw && P->tc_capc >= capc) return LAGR_OK;
+  dev_free(G->u_dplus, s);
   dev_free(G->u_colidx, s);
-  G->u_rowptr = G->u_colidx = nullptr;
-  dev_free(P->tc_dplus, s);
+  G->u_dplus = G->u_colidx = nullptr;
   dev_free(P->tc_listw, s);
   dev_free(P->tc_listwh, s);
   dev_free(P->tc_listc, s);
-  dev_free(P->tc_scan, s);
   dev_free(P->tc_rank, s);
   dev_free(P->tc_sortbuf, s);
   dev_free(P->tc_radix, s);
   dev_free(P->tc_radix_scan, s);
-  P->tc_scan = nullptr;
   P->tc_radix_scan = nullptr;
-  P->tc_dplus = P->tc_listw = P->tc_rank = P->tc_sortbuf = P->tc_radix = nullptr;
+  P->tc_listw = P->tc_rank = P->tc_sortbuf = P->tc_radix = nullptr;
   P->tc_listc = nullptr;
   P->tc_listwh = nullptr;
   P->tc_capc = 0;
@@ -625,16 +583,14 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
   LAGR_TRY(lagr_property_row_degree(G, s, msg));
   LAGR_TRY(lagr_property_AT(G, s, msg));  // undirected: A' aliases A, so the row plan is shared
   LAGR_TRY(row_plan(&P->pr_at, G->rowptr, n, s, msg));
-  LAGR_TRY(alloc_n(&P->tc_dplus, (size_t)n + 1, s, msg, "d+"));
-  LAGR_TRY(alloc_n(&G->u_rowptr, (size_t)n + 1, s, msg, "U row pointers"));
-  LAGR_TRY(alloc_n(&G->u_colidx, (size_t)(nnz / 2 + 1), s, msg, "U column indices"));
+  LAGR_TRY(alloc_n(&G->u_dplus, (size_t)n + 1, s, msg, "d+"));
+  LAGR_TRY(alloc_n(&G->u_colidx, (size_t)(nnz > 0 ? nnz : 1), s, msg, "U column indices"));
   LAGR_TRY(alloc_n(&P->tc_listw, (size_t)n + 1, s, msg, "warp anchors"));
   // warp anchors cut into items: ceil(deg / TCW_CHUNK) <= 2 deg / TCW_CHUNK items each (deg > TCW_CHUNK)
   const int64_t capwh = 2 * (nnz / TCW_CHUNK) + 64;
   LAGR_TRY(alloc_n(&P->tc_listwh, (size_t)capwh, s, msg, "warp anchor items"));
   P->tc_capwh = capwh;
   LAGR_TRY(alloc_n(&P->tc_listc, (size_t)capc, s, msg, "CTA anchors"));
-  LAGR_TRY(alloc_n(&P->tc_scan, (size_t)scan_scratch_len(n), s, msg, "scan scratch"));
   LAGR_TRY(alloc_n(&P->tc_rank, (size_t)n + 1, s, msg, "degree ranks"));
   LAGR_TRY(alloc_n(&P->tc_sortbuf, 4 * (size_t)n + 4, s, msg, "rank sort buffers"));
   LAGR_TRY(alloc_n(&P->tc_radix, (size_t)radix_scratch_len(n), s, msg, "radix scratch"));
@@ -650,7 +606,6 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
               unsigned long long *counts, bool orient, cudaStream_t s, char *msg) {
   const int32_t n = G->n;
   const int64_t nnz = G->nnz;
-  const int64_t ucap = nnz / 2 + 1;
   if (orient) {
     LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal, 0, LAGR_NSCAL * sizeof(int64_t), s));
     if (method == LAGR_TC_AUTO) {
@@ -667,19 +622,11 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
     LAGR_TRY(radix_sort_pairs(keys, vals, tk, tv, n, bits, s, msg, P->tc_radix, P->tc_radix_scan));
     tc_rank_scatter<<<grid_for(n, 256), 256, 0, s>>>(vals, n, P->dscal, P->tc_rank);
     const RowPlan &rp = P->pr_at;
-    tc_orient_rows<false><<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, P->dscal, P->tc_dplus,
-                                                   nullptr, nullptr, 0);
+    tc_orient_rows<<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, G->u_dplus, G->u_colidx);
     if (rp.nheavy > 0)
-      tc_orient_count_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, P->tc_dplus, rp.heavy,
-                                                    rp.nheavy);
-    LAGR_LAUNCH_CHECK();
-    LAGR_TRY(exclusive_scan(P->tc_dplus, G->u_rowptr, n, s, msg, P->tc_scan));
-    tc_orient_rows<true><<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, P->dscal, nullptr,
-                                                  G->u_rowptr, G->u_colidx, ucap);
-    if (rp.nheavy > 0)
-      tc_orient_fill_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, P->dscal, G->u_rowptr,
-                                                   G->u_colidx, ucap, rp.heavy, rp.nheavy);
-    tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, P->tc_dplus, n, P->tc_listw, P->tc_listwh,
+      tc_orient_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, G->u_dplus, G->u_colidx, rp.heavy,
+                                              rp.nheavy);
+    tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, P->tc_listw, P->tc_listwh,
                                                  P->tc_capwh, P->tc_listc, P->tc_capc, P->dscal, prm.wmax,
                                                  prm.chunk);
     LAGR_LAUNCH_CHECK();
@@ -697,14 +644,14 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
   const int32_t w0w = n > (1 << TCW_WIN_LOG) ? n - (1 << TCW_WIN_LOG) : 0;
   {
     KTimer kt(TK_TC_CTA, s);
-    tc_count_cta<<<152 * 4, TCC_THREADS, TCC_SMEM, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx, P->tc_dplus,
+    tc_count_cta<<<152 * 4, TCC_THREADS, TCC_SMEM, s>>>(G->rowptr, G->colidx, G->rowptr, G->u_colidx, G->u_dplus,
                                                         P->tc_rank, P->tc_listc, P->dscal, w0c, voff, ngraphs, counts,
                                                         prm.chunk, P->tc_capc);
   }
   {
     KTimer kt(TK_TC_WARP, s);
-    tc_count_warp<<<152 * 4, TCW_WARPS * 32, TCW_SMEM, s>>>(G->rowptr, G->colidx, G->u_rowptr, G->u_colidx,
-                                                            P->tc_dplus, P->tc_rank, P->tc_listw, n, P->tc_listwh,
+    tc_count_warp<<<152 * 4, TCW_WARPS * 32, TCW_SMEM, s>>>(G->rowptr, G->colidx, G->rowptr, G->u_colidx,
+                                                            G->u_dplus, P->tc_rank, P->tc_listw, n, P->tc_listwh,
                                                             P->tc_capwh, P->dscal, w0w,
                                                             voff, ngraphs, counts);
   }
@@ -741,7 +688,7 @@ extern "C" int lagr_tc(uint64_t *ntriangles, lagr_graph G, int32_t method, void 
   Priv *P = nullptr;
   LAGR_TRY(priv_get(G, s, msg, &P));
   const TcParams prm = tc_default_params();
-  const bool cached = G->u_rowptr && G->u_order == method && P->tc_listw;
+  const bool cached = G->u_colidx && G->u_order == method && P->tc_listw;
   LAGR_TRY(tc_alloc(G, P, prm, s, msg));
   LAGR_TRY(tc_launch(G, P, method, prm, nullptr, 1, tc_total_slot(P), !cached, s, msg));
   G->u_order = method;
