@@ -233,12 +233,18 @@ def run_gpu(args):
     d2h = sum(t.numel() * 4 for t in hosts[0]) + 8
     copy = torch.cuda.Stream(dev)
 
+    up_marks, down_marks = [], []  # copy-stream events around every upload and download
+
     def upload():
         with torch.cuda.stream(copy):
+            a, b = ev(), ev()
+            a.record(copy)
             rp_d = rp_h.to(dev, non_blocking=True)
             ci_d = ci_h.to(dev, non_blocking=True)
             ready = torch.cuda.Event()
             ready.record(copy)
+            b.record(copy)
+            up_marks.append((a, b))
         return rp_d, ci_d, ready
 
     e_start, e_end = ev(), ev()
@@ -261,8 +267,12 @@ def run_gpu(args):
         done.record(stream)
         with torch.cuda.stream(copy):
             copy.wait_event(done)
+            a, b = ev(), ev()
+            a.record(copy)
             for h, d in zip(hosts[k % 2], outs[k % 2]):
                 h.copy_(d, non_blocking=True)
+            b.record(copy)
+            down_marks.append((a, b))
             freed[k % 2] = torch.cuda.Event()
             freed[k % 2].record(copy)
     for f in freed:
@@ -271,6 +281,8 @@ def run_gpu(args):
     e_end.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), world) / args.steps
+    up_ms = statistics.median(a.elapsed_time(b) for a, b in up_marks) if up_marks else 0.0
+    down_ms = statistics.median(a.elapsed_time(b) for a, b in down_marks) if down_marks else 0.0
     if args.steps > 0 and only in ("all", "bfs"):  # the downloaded levels are the computed ones
         last = (args.steps - 1) % 2
         assert torch.equal(hosts[last][0][0], outs[last][0][0].cpu())
@@ -306,7 +318,8 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks,
             "e2e": {"value": round(job_throughput(edges_per_step, world, e2e_ms) / 1e9, 4), "unit": "GTEPS",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": round(e2e_ms, 3), "h2d_ms": round(up_ms, 3), "d2h_ms": round(down_ms, 3)},
             "gpu_launches": launches_timed,
             "components": {
                 "triangles": t_tri, "tc_ms": round(tc_ms, 3),

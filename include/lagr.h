@@ -139,12 +139,26 @@ typedef lagr_graph_struct *lagr_graph;
  * allocation of the library goes through alloc(bytes, stream, ctx) and
  * free_(ptr, stream, ctx).  alloc returns NULL on failure, which the calling
  * function reports as LAGR_ERR_OUT_OF_MEMORY.  Passing NULLs restores the
- * default (cudaMallocAsync / cudaFreeAsync on the call's stream).  Not
- * thread-safe: set it before the first call.
+ * default: stream-ordered allocation (cudaMallocFromPoolAsync / cudaFreeAsync
+ * on the call's stream) from a memory pool the library creates per device,
+ * which keeps freed memory for later calls instead of returning it to the
+ * driver at the next synchronisation.  Not thread-safe: set it before the
+ * first call.
  */
 typedef void *(*lagr_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*lagr_free_fn)(void *ptr, void *stream, void *ctx);
 int lagr_set_allocator(lagr_alloc_fn alloc, lagr_free_fn free_, void *ctx);
+
+/*
+ * Hand memory the default allocator keeps back to the driver (no paper
+ * counterpart; the counterpart of LAGraph's finalize for the memory pools):
+ * every per-device pool of the library is trimmed to at most keep_bytes of
+ * free memory (cudaMemPoolTrimTo; memory of live graphs, or freed by work
+ * still queued on a stream, stays), and the recycled pinned host scalars of
+ * freed graphs are released.  Thread-safe.  Returns LAGR_ERR_CUDA (with the
+ * device in msg) if a trim fails.
+ */
+int lagr_release_memory(uint64_t keep_bytes, char *msg);
 
 /*
  * Create a graph from a device CSR (the "move" constructor of Sec. II-A,

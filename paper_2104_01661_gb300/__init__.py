@@ -96,6 +96,7 @@ _SIGNATURES = {
     "lagr_timing_read": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)], ctypes.c_int),
     "lagr_timing_reset": ([], ctypes.c_int),
     "lagr_set_allocator": ([_vp, _vp, _vp], ctypes.c_int),
+    "lagr_release_memory": ([ctypes.c_uint64, _str], ctypes.c_int),
     "lagr_graph_new": ([ctypes.POINTER(_G), _i32, _i64, _vp, _vp, _vp, _i32, _str], ctypes.c_int),
     "lagr_graph_free": ([ctypes.POINTER(_G), _vp, _str], ctypes.c_int),
     "lagr_delete_properties": ([_G, _vp, _str], ctypes.c_int),
@@ -462,6 +463,12 @@ def timing_read(kernel: str):
     if rc < 0:
         raise LagrError(rc, f"unknown kernel {kernel!r} or an event failed", "lagr_timing_read")
     return float(ms.value), int(cnt.value)
+
+
+def lagr_release_memory(keep_bytes: int = 0) -> None:
+    """Trim the library's device memory pools to ``keep_bytes`` of free memory each."""
+    msg = _msg()
+    _check(load_library().lagr_release_memory(int(keep_bytes), msg), msg, "lagr_release_memory")
 
 
 def version() -> str:

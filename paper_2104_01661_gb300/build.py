@@ -69,8 +69,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         objs = list(ex.map(one, _sources()))
     tmp = LIB + f".tmp{os.getpid()}"
     # the wrap routes every kernel launch of the library through its launch counter
+    # --no-undefined: a symbol no object defines fails the link, not the first load
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-Xlinker",
-                                                       "--wrap=__cudaLaunchKernel"]
+                                                       "--wrap=__cudaLaunchKernel", "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -42,6 +42,12 @@ enum BfsSlot {
   B_NSLOT = 8
 };
 
+// the counters, also stored into the caller's pinned host mirror (device-mapped), so that the host
+// reads them after a stream synchronisation without a copy
+__device__ __forceinline__ void mirror_counters(const int64_t *c, int64_t *hm) {
+  for (int i = 0; i < B_NSLOT; i++) hm[i] = c[i];
+}
+
 __global__ void bfs_init(int32_t n, int32_t *__restrict__ level, int32_t *__restrict__ parent,
                          uint32_t *__restrict__ visited, int64_t nwords) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -54,7 +60,7 @@ __global__ void bfs_init(int32_t n, int32_t *__restrict__ level, int32_t *__rest
 
 __global__ void bfs_seed(const int32_t *__restrict__ rowptr, int64_t nnz, int32_t src, int32_t *__restrict__ level,
                          int32_t *__restrict__ parent, uint32_t *__restrict__ visited, int32_t *__restrict__ qa,
-                         int64_t *__restrict__ c) {
+                         int64_t *__restrict__ c, int64_t *hm) {
   if (level) level[src] = 0;
   if (parent) parent[src] = src;
   visited[src >> 5] |= 1u << (src & 31);
@@ -64,6 +70,7 @@ __global__ void bfs_seed(const int32_t *__restrict__ rowptr, int64_t nnz, int32_
   c[B_NQ] = 1;
   c[B_MF] = d;
   c[B_MU] = nnz - d;
+  if (hm) mirror_counters(c, hm);
 }
 
 // Claim v for the frontier vertex u at level lev.  Returns true when this thread won v.
@@ -300,7 +307,8 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(SMALL_THREADS, 1)
     bfs_push_small(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
                    int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
-                   int32_t *__restrict__ parent, int64_t *__restrict__ c, int32_t max_level, int allow_pull) {
+                   int32_t *__restrict__ parent, int64_t *__restrict__ c, int32_t max_level, int allow_pull,
+                   int64_t *hm) {
   __shared__ unsigned long long s_next, s_mdeg;
   __shared__ int32_t s_big[SMALL_MAX];  // frontier vertices with long rows (the caller keeps nq <= SMALL_MAX)
   __shared__ int s_nbig;
@@ -347,6 +355,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1)
     c[B_MU] = mu;
     c[B_MF] = mf;
     c[B_EXIT] = exit_reason;
+    if (hm) mirror_counters(c, hm);
   }
 }
 
@@ -443,7 +452,7 @@ __global__ void __launch_bounds__(BFS_THREADS)
 }
 
 // after a level: the next frontier becomes the current one
-__global__ void bfs_advance(int64_t *__restrict__ c, int flip) {
+__global__ void bfs_advance(int64_t *__restrict__ c, int flip, int64_t *hm) {
   c[B_NQ] = c[B_NEXT];
   c[B_MF] = c[B_MNEXT];
   c[B_MU] -= c[B_MNEXT];
@@ -451,6 +460,7 @@ __global__ void bfs_advance(int64_t *__restrict__ c, int flip) {
   if (flip) c[B_PAR] ^= 1;
   c[B_NEXT] = 0;
   c[B_MNEXT] = 0;
+  if (hm) mirror_counters(c, hm);
 }
 
 __global__ void bfs_set_par(int64_t *__restrict__ c, int par) { c[B_PAR] = par; }
@@ -487,14 +497,18 @@ __global__ void bfs64_init(int32_t n, int32_t k, int32_t *__restrict__ level, un
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) level[i] = -1;
 }
 
-__global__ void bfs64_seed(int32_t n, int32_t k, const int32_t *__restrict__ src, const int32_t *__restrict__ rowptr,
+struct Sources64 {
+  int32_t v[64];
+};
+
+__global__ void bfs64_seed(int32_t n, int32_t k, const Sources64 src, const int32_t *__restrict__ rowptr,
                            int32_t *__restrict__ level, unsigned long long *__restrict__ seen,
                            unsigned long long *__restrict__ front, int32_t *__restrict__ flist,
                            int64_t *__restrict__ cnt) {
   if (threadIdx.x != 0) return;
   int64_t nf = 0, mf = 0;
   for (int s = 0; s < k; s++) {
-    const int32_t v = src[s];
+    const int32_t v = src.v[s];
     if (front[v] == 0) {
       flist[nf++] = v;
       mf += rowptr[v + 1] - rowptr[v];
@@ -753,12 +767,12 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
   LAGR_TRY(offs.alloc((size_t)n + 1, msg, "frontier edge offsets"));
   LAGR_TRY(cnt.alloc(B_NSLOT, msg, "BFS counters"));
   bfs_init<<<grid_for(n, 256), 256, 0, s>>>(n, level, parent, visited.p, nwords);
-  bfs_seed<<<1, 1, 0, s>>>(G->rowptr, G->nnz, src, level, parent, visited.p, qa.p, cnt.p);
+  bfs_seed<<<1, 1, 0, s>>>(G->rowptr, G->nnz, src, level, parent, visited.p, qa.p, cnt.p, P->hscal_dev);
   LAGR_LAUNCH_CHECK();
 
-  int64_t *h = P->hscal;  // pinned mirror of the counters
+  // pinned mirror of the counters: bfs_seed, bfs_push_small and bfs_advance store them there
+  const int64_t *h = P->hscal;
   auto sync_counters = [&]() -> int {
-    LAGR_CUDA_TRY(cudaMemcpyAsync(h, cnt.p, B_NSLOT * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     LAGR_CUDA_TRY(cudaStreamSynchronize(s));
     return LAGR_OK;
   };
@@ -799,7 +813,7 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
         {
           KTimer kt(TK_BFS_SMALL, s);
           bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level, parent,
-                                                     cnt.p, n, push_only ? 0 : 1);
+                                                     cnt.p, n, push_only ? 0 : 1, P->hscal_dev);
         }
         LAGR_LAUNCH_CHECK();
         LAGR_TRY(sync_counters());
@@ -827,7 +841,7 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
           bfs_push_lb<<<(unsigned)(nchunks > 0 ? nchunks : 1), 256, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, offs.p,
                                                                            visited.p, nbits.p, level, parent, cnt.p);
         }
-        bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0);
+        bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0, P->hscal_dev);
         LAGR_LAUNCH_CHECK();
         uint32_t *t = fbits.p;
         fbits.p = nbits.p;
@@ -852,7 +866,7 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
                                                                           fbits.p, nbits.p, visited.p, level, parent,
                                                                           cnt.p);
     }
-    bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0);
+    bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0, P->hscal_dev);
     LAGR_LAUNCH_CHECK();
     {
       uint32_t *t = fbits.p;
@@ -899,31 +913,29 @@ extern "C" int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src
   const RowPlan &rp = P->pr_at;
   const int32_t n = G->n;
   Temp<unsigned long long> seen(s), fa(s), fb(s), acc(s);
-  Temp<int32_t> dsrc(s), la(s), lb(s), touched(s), fdeg(s), offs(s);
+  Temp<int32_t> la(s), lb(s), touched(s), fdeg(s), offs(s);
   Temp<int64_t> cnt(s);
   LAGR_TRY(seen.alloc(n, msg, "seen words"));
   LAGR_TRY(fa.alloc(n, msg, "frontier words"));
   LAGR_TRY(fb.alloc(n, msg, "frontier words"));
   LAGR_TRY(acc.alloc(n, msg, "push words"));
-  LAGR_TRY(dsrc.alloc(k, msg, "sources"));
   LAGR_TRY(la.alloc(n, msg, "frontier list"));
   LAGR_TRY(lb.alloc(n, msg, "frontier list"));
   LAGR_TRY(touched.alloc(n, msg, "touched list"));
   LAGR_TRY(fdeg.alloc(n, msg, "frontier degrees"));
   LAGR_TRY(offs.alloc((size_t)n + 1, msg, "frontier offsets"));
   LAGR_TRY(cnt.alloc(2 * S64_NSLOT, msg, "counters"));
-  // the sources travel through the pinned mirror so the copy is asynchronous
-  memcpy(P->hscal, src, (size_t)k * sizeof(int32_t));
-  LAGR_CUDA_TRY(cudaMemcpyAsync(dsrc.p, P->hscal, (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  // the sources travel as a kernel argument (no copy)
+  Sources64 sv;
+  for (int i = 0; i < 64; i++) sv.v[i] = i < k ? src[i] : 0;
   const unsigned long long kmask = (k == 64) ? ~0ull : ((1ull << k) - 1);
   bfs64_init<<<grid_for((int64_t)k * n, 256), 256, 0, s>>>(n, k, level, seen.p, fa.p, fb.p, acc.p);
-  bfs64_seed<<<1, 32, 0, s>>>(n, k, dsrc.p, G->rowptr, level, seen.p, fa.p, la.p, cnt.p);
+  bfs64_seed<<<1, 32, 0, s>>>(n, k, sv, G->rowptr, level, seen.p, fa.p, la.p, cnt.p);
   LAGR_LAUNCH_CHECK();
   unsigned long long *front = fa.p, *fnext = fb.p;
   int32_t *flist = la.p, *nflist = lb.p;
   int64_t *cur = cnt.p, *nxt = cnt.p + S64_NSLOT;  // counters of this level / the next
-  LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, cur, S64_NSLOT * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  LAGR_TRY(fetch_to_host(P->hscal, cur, S64_NSLOT * sizeof(int64_t), s, msg));
   int64_t nf = P->hscal[S64_NF], mf = P->hscal[S64_MF];
   int32_t lev = 0;
   const int nhb = rp.nheavy < 152 ? rp.nheavy : 152;
@@ -952,8 +964,7 @@ extern "C" int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src
     }
     bfs64_clear<<<grid_for(nf, 256), 256, 0, s>>>(flist, (int32_t)nf, front);
     LAGR_LAUNCH_CHECK();
-    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, nxt, S64_NSLOT * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+    LAGR_TRY(fetch_to_host(P->hscal, nxt, S64_NSLOT * sizeof(int64_t), s, msg));
     nf = P->hscal[S64_NF];
     mf = P->hscal[S64_MF];
     std::swap(front, fnext);
@@ -1056,7 +1067,7 @@ extern "C" int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth,
 
   // bfs_init clears the visited words and the outputs, bfs_seed resets every counter
   bfs_init<<<grid_for(n, 256), 256, 0, s>>>(n, level, parent, visited, nwords);
-  bfs_seed<<<1, 1, 0, s>>>(rowptr, nnz, src, level, parent, visited, qa, cnt);
+  bfs_seed<<<1, 1, 0, s>>>(rowptr, nnz, src, level, parent, visited, qa, cnt, nullptr);
   LAGR_LAUNCH_CHECK();
   int64_t h[B_NSLOT];
   auto sync_counters = [&]() -> int {
@@ -1090,7 +1101,8 @@ extern "C" int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth,
         rep = 0;
       }
       if (nq <= SMALL_MAX && mf <= SMALL_EDGES) {
-        bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(rowptr, colidx, qa, qb, visited, level, parent, cnt, n, 1);
+        bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(rowptr, colidx, qa, qb, visited, level, parent, cnt, n, 1,
+                                                   nullptr);
         LAGR_LAUNCH_CHECK();
         LAGR_TRY(sync_counters());
         if (h[B_EXIT] == 4 || (int32_t)h[B_LEV] <= lev) {
@@ -1102,7 +1114,7 @@ extern "C" int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth,
         LAGR_CUDA_TRY(cudaMemsetAsync(nbits, 0, nwords * sizeof(uint32_t), s));
         bfs_push<<<grid_for(nq, BFS_THREADS), BFS_THREADS, 0, s>>>(rowptr, colidx, qa, qb, visited, nbits, level,
                                                                    parent, cnt);
-        bfs_advance<<<1, 1, 0, s>>>(cnt, 0);
+        bfs_advance<<<1, 1, 0, s>>>(cnt, 0, nullptr);
         LAGR_LAUNCH_CHECK();
         uint32_t *t = fbits;
         fbits = nbits;
@@ -1122,7 +1134,7 @@ extern "C" int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth,
     // the graph is undirected, so A' = A: the pull scans the rows of A
     bfs_pull<<<grid_for(nwords * 32, BFS_THREADS), BFS_THREADS, 0, s>>>(rowptr, colidx, rowptr, n, fbits, nbits,
                                                                         visited, level, parent, cnt);
-    bfs_advance<<<1, 1, 0, s>>>(cnt, 0);
+    bfs_advance<<<1, 1, 0, s>>>(cnt, 0, nullptr);
     LAGR_LAUNCH_CHECK();
     uint32_t *t = fbits;
     fbits = nbits;

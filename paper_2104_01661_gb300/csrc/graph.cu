@@ -44,14 +44,147 @@ static lagr_alloc_fn g_alloc = nullptr;
 static lagr_free_fn g_free = nullptr;
 static void *g_ctx = nullptr;
 
+// The default allocator takes device memory from a pool of the library's own (one per device) that
+// keeps what is freed instead of handing it back at the next synchronisation, as a pool with the
+// default release threshold does: the entry points synchronise often (BFS levels, PageRank checks),
+// and re-mapping the work space of every call would cost more than the work on small graphs.
+// lagr_release_memory trims the pools.
+constexpr int MAX_DEVICES = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[MAX_DEVICES] = {};
+
+static cudaMemPool_t lib_pool() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEVICES) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[d]) {
+    cudaMemPoolProps pr;
+    memset(&pr, 0, sizeof(pr));
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.handleTypes = cudaMemHandleTypeNone;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = d;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &pr) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) cudaGetLastError();
+    g_pool[d] = pool;
+  }
+  return g_pool[d];
+}
+
 void *dev_alloc(size_t bytes, cudaStream_t s) {
   if (g_alloc) return g_alloc(bytes, (void *)s, g_ctx);
   void *p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+  cudaMemPool_t pool = lib_pool();
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
     cudaGetLastError();  // clear the sticky-free error state of a failed allocation
     return nullptr;
   }
   return p;
+}
+
+// Pinned host mirrors of the device scalars (LAGR_NHOST int64 each, with their device-mapped
+// addresses), recycled between graphs and calls: allocating and freeing pinned memory per graph
+// costs a device-wide synchronisation in the free.
+struct HostBlock {
+  int64_t *h, *d;
+};
+static std::mutex g_host_mu;
+static std::vector<HostBlock> g_host_free;
+
+static bool host_block_get(HostBlock *b) {
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    if (!g_host_free.empty()) {
+      *b = g_host_free.back();
+      g_host_free.pop_back();
+      return true;
+    }
+  }
+  int64_t *h = nullptr;
+  void *d = nullptr;
+  if (cudaHostAlloc((void **)&h, LAGR_NHOST * sizeof(int64_t), cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(h);
+    return false;
+  }
+  *b = HostBlock{h, (int64_t *)d};
+  return true;
+}
+
+static void host_block_put(HostBlock b) {
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  g_host_free.push_back(b);
+}
+
+struct FetchList {
+  const int32_t *p[8];
+};
+
+__global__ void fetch_words_kernel(const uint32_t *__restrict__ src, int nwords, uint32_t *dst) {
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) dst[i] = src[i];
+}
+
+__global__ void fetch_list_kernel(FetchList l, int count, int32_t *dst) {
+  if ((int)threadIdx.x < count) dst[threadIdx.x] = *l.p[threadIdx.x];
+}
+
+int fetch_to_host(void *dst, const void *dsrc, size_t bytes, cudaStream_t s, char *msg) {
+  if (bytes % 4 != 0 || bytes > LAGR_NHOST * sizeof(int64_t)) {
+    set_msg(msg, "internal: fetch of %zu bytes", bytes);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  HostBlock b;
+  if (!host_block_get(&b)) {
+    set_msg(msg, "out of pinned host memory");
+    return LAGR_ERR_OUT_OF_MEMORY;
+  }
+  fetch_words_kernel<<<1, 32, 0, s>>>((const uint32_t *)dsrc, (int)(bytes / 4), (uint32_t *)b.d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_msg(msg, "CUDA error: %s", cudaGetErrorString(e));
+    return LAGR_ERR_CUDA;  // the block may still be written: it is not recycled
+  }
+  memcpy(dst, b.h, bytes);
+  host_block_put(b);
+  return LAGR_OK;
+}
+
+int fetch_i32s(int32_t *dst, const int32_t *const *srcs, int count, cudaStream_t s, char *msg) {
+  if (count < 1 || count > 8) {
+    set_msg(msg, "internal: fetch of %d scalars", count);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  HostBlock b;
+  if (!host_block_get(&b)) {
+    set_msg(msg, "out of pinned host memory");
+    return LAGR_ERR_OUT_OF_MEMORY;
+  }
+  FetchList l;
+  for (int i = 0; i < 8; i++) l.p[i] = i < count ? srcs[i] : nullptr;
+  fetch_list_kernel<<<1, 32, 0, s>>>(l, count, (int32_t *)b.d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_msg(msg, "CUDA error: %s", cudaGetErrorString(e));
+    return LAGR_ERR_CUDA;
+  }
+  memcpy(dst, b.h, (size_t)count * sizeof(int32_t));
+  host_block_put(b);
+  return LAGR_OK;
 }
 
 void dev_free(void *p, cudaStream_t s) {
@@ -76,7 +209,13 @@ int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out) {
     LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal, 0, LAGR_NSCAL * sizeof(int64_t), s));
   }
   if (!P->hscal) {
-    LAGR_CUDA_TRY(cudaMallocHost(&P->hscal, LAGR_NHOST * sizeof(int64_t)));
+    HostBlock b;
+    if (!host_block_get(&b)) {
+      set_msg(msg, "out of pinned host memory (%d bytes)", (int)(LAGR_NHOST * sizeof(int64_t)));
+      return LAGR_ERR_OUT_OF_MEMORY;
+    }
+    P->hscal = b.h;
+    P->hscal_dev = b.d;
   }
   *out = P;
   return LAGR_OK;
@@ -112,8 +251,9 @@ void priv_release(lagr_graph G, cudaStream_t s) {
   }
   dev_free(P->dscal, s);
   if (P->hscal) {
-    cudaStreamSynchronize(s);
-    cudaFreeHost(P->hscal);
+    // every reader of hscal synchronises first; this covers a call that returned early
+    if (cudaStreamSynchronize(s) == cudaSuccess) host_block_put(HostBlock{P->hscal, P->hscal_dev});
+    else cudaGetLastError();
   }
   delete P;
   G->priv = nullptr;
@@ -311,6 +451,26 @@ int lagr_set_allocator(lagr_alloc_fn alloc, lagr_free_fn free_, void *ctx) {
   return LAGR_OK;
 }
 
+int lagr_release_memory(uint64_t keep_bytes, char *msg) {
+  set_msg(msg, "");
+  int rc = LAGR_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int d = 0; d < MAX_DEVICES; d++)
+      if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], (size_t)keep_bytes) != cudaSuccess) {
+        set_msg(msg, "cudaMemPoolTrimTo failed on device %d: %s", d, cudaGetErrorString(cudaGetLastError()));
+        rc = LAGR_ERR_CUDA;
+      }
+  }
+  std::vector<HostBlock> held;
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    held.swap(g_host_free);
+  }
+  for (const HostBlock &b : held) cudaFreeHost(b.h);
+  return rc;
+}
+
 int lagr_graph_new(lagr_graph *G, int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
                    const float *val, int32_t kind, char *msg) {
   if (!G) {
@@ -455,8 +615,7 @@ int lagr_graph_check(lagr_graph G, void *stream, char *msg) {
   LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal, 0, 2 * sizeof(int64_t), s));
   check_rowptr<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, n, G->nnz, P->dscal);
   LAGR_LAUNCH_CHECK();
-  LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  LAGR_TRY(fetch_to_host(P->hscal, P->dscal, 2 * sizeof(int64_t), s, msg));
   int64_t bad = P->hscal[0];
   if (bad) {
     set_msg(msg, "invalid row pointers:%s%s%s", (bad & BAD_ROWPTR0) ? " rowptr[0] != 0" : "",
@@ -465,8 +624,7 @@ int lagr_graph_check(lagr_graph G, void *stream, char *msg) {
   }
   if (n > 0) check_rows<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(G->rowptr, G->colidx, n, P->dscal);
   LAGR_LAUNCH_CHECK();
-  LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  LAGR_TRY(fetch_to_host(P->hscal, P->dscal, 2 * sizeof(int64_t), s, msg));
   bad = P->hscal[0];
   G->ndiag = P->hscal[1];
   if (bad) {
@@ -484,8 +642,7 @@ int lagr_graph_check(lagr_graph G, void *stream, char *msg) {
     compare_arrays<<<grid_for(n + 1, 256), 256, 0, s>>>(G->rowptr, rp.p, (int64_t)n + 1, P->dscal);
     if (G->nnz > 0) compare_arrays<<<grid_for(G->nnz, 256), 256, 0, s>>>(G->colidx, ci.p, G->nnz, P->dscal);
     LAGR_LAUNCH_CHECK();
-    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+    LAGR_TRY(fetch_to_host(P->hscal, P->dscal, sizeof(int64_t), s, msg));
   }
   const int symmetric = P->hscal[0] == 0;
   G->a_pattern_is_symmetric = symmetric;

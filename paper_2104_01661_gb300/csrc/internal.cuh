@@ -105,7 +105,8 @@ constexpr int ROW_HCHUNK = 8192;
 struct Priv {
   // small device scratch: counters and flags used by every algorithm
   int64_t *dscal = nullptr;  // LAGR_NSCAL int64 slots
-  int64_t *hscal = nullptr;  // pinned host mirror
+  int64_t *hscal = nullptr;      // pinned host mirror (LAGR_NHOST slots) ...
+  int64_t *hscal_dev = nullptr;  // ... and its address for kernels, which write it directly
   // triangle counting: anchors of the warp class and CTA-class items (x, first neighbour)
   int32_t *tc_listw = nullptr;
   int2 *tc_listc = nullptr;
@@ -134,11 +135,21 @@ enum ScalarSlot {
   SC_COUNT7 = 8,
   SC_COUNT8 = 9,
   SC_COUNT9 = 10,
+  SC_COUNT10 = 11,
+  SC_COUNT11 = 12,
   LAGR_NSCAL = 16,
   LAGR_NHOST = 64  // int64 slots of the pinned host mirror (also stages up to 64 int32 sources)
 };
 
 int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out);
+
+// Small device-to-host reads that bypass the copy engines (a large copy queued on another stream
+// would delay them): a one-warp kernel stores the values into pinned, device-mapped host memory,
+// the stream is synchronised, and the values are copied out.  fetch_to_host reads `bytes`
+// contiguous bytes (a multiple of 4, at most LAGR_NHOST * 8); fetch_i32s gathers `count` (<= 8)
+// scalars from separate addresses.
+int fetch_to_host(void *dst, const void *dsrc, size_t bytes, cudaStream_t s, char *msg);
+int fetch_i32s(int32_t *dst, const int32_t *const *srcs, int count, cudaStream_t s, char *msg);
 
 // build (once; no-op when pl->nblk >= 0) the row plan of a CSR.  Synchronises the stream.
 int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg, int32_t units = ROW_UNITS,
@@ -209,10 +220,6 @@ int radix_sort_pairs(int32_t *keys, int32_t *vals, int32_t *tmp_k, int32_t *tmp_
                      int bits, cudaStream_t s, char *msg, int32_t *scratch = nullptr,
                      int64_t *scan_scratch = nullptr);
 
-// stable compaction of the indices i in [0, n) with deg(i) > threshold (deg from rowptr);
-// writes *list (allocated here) and its length (host value; synchronises the stream).
-int heavy_rows(const int32_t *rowptr, int32_t n, int32_t threshold, int32_t **list, int32_t *count,
-               cudaStream_t s, char *msg);
 
 // CSR -> CSC (A' by row) with rows sorted; at_val may be NULL when val is NULL.
 int transpose_csr(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,

@@ -565,9 +565,7 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const in
     launched += chunk;
     static_assert(PR_STATE_HOST == offsetof(PrState, fold) && PR_STATE_HOST <= LAGR_NHOST * sizeof(int64_t),
                   "host part of the state");
-    LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, st, PR_STATE_HOST, cudaMemcpyDeviceToHost, s));
-    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
-    memcpy(&host, P->hscal, PR_STATE_HOST);
+    LAGR_TRY(fetch_to_host(&host, st, PR_STATE_HOST, s, msg));
     if (host.done) break;
   }
   if (host.iters & 1) LAGR_CUDA_TRY(cudaMemcpyAsync(buf0, x[1], (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s));

@@ -157,11 +157,6 @@ __global__ void radix_scatter(const int32_t *__restrict__ keys, const int32_t *_
 
 // ---- heavy-row compaction ---------------------------------------------------------------------
 
-__global__ void mark_heavy(const int32_t *__restrict__ rowptr, int32_t n, int32_t threshold, int32_t *__restrict__ flag) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    flag[i] = (rowptr[i + 1] - rowptr[i]) > threshold;
-}
-
 __global__ void scatter_heavy(const int32_t *__restrict__ flag, const int32_t *__restrict__ pos, int32_t n,
                               int32_t *__restrict__ list) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -202,11 +197,46 @@ __global__ void gather_transpose(const int32_t *__restrict__ perm, const int32_t
 
 // ---- row plan -----------------------------------------------------------------------------------
 
-__global__ void light_degree(const int32_t *__restrict__ rowptr, int32_t n, int32_t heavy,
-                             int32_t *__restrict__ ld) {
+// per row: 1 if it is heavy (more than `heavy` entries), and its light degree (0 for a heavy row)
+__global__ void row_classes(const int32_t *__restrict__ rowptr, int32_t n, int32_t heavy, int32_t *__restrict__ hflag,
+                            int32_t *__restrict__ ld) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t d = rowptr[i + 1] - rowptr[i];
+    hflag[i] = d > heavy;
     ld[i] = d <= heavy ? d : 0;
+  }
+}
+
+// every block start: the rows b0[0 .. nb0-1] (below n), each heavy row and the row after it
+__global__ void mark_cuts(const int32_t *__restrict__ b0, int32_t nb0, const int32_t *__restrict__ heavy, int32_t nh,
+                          int32_t n, int32_t *__restrict__ mark) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb0; i += stride)
+    if (b0[i] < n) mark[b0[i]] = 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nh; i += stride) {
+    mark[heavy[i]] = 1;
+    if (heavy[i] + 1 < n) mark[heavy[i] + 1] = 1;
+  }
+}
+
+// the marked rows in order become blk[]; a block that starts at a heavy row is that row alone
+__global__ void scatter_blocks(const int32_t *__restrict__ mark, const int32_t *__restrict__ mpos,
+                               const int32_t *__restrict__ rowptr, int32_t n, int32_t heavy,
+                               int32_t *__restrict__ blk, uint8_t *__restrict__ hblk) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+    if (mark[r]) {
+      blk[mpos[r]] = (int32_t)r;
+      hblk[mpos[r]] = (rowptr[r + 1] - rowptr[r]) > heavy;
+    }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (n == 0) {  // one empty block
+      blk[0] = 0;
+      blk[1] = 0;
+      hblk[0] = 0;
+    } else {
+      blk[mpos[n]] = n;
+    }
   }
 }
 
@@ -305,28 +335,6 @@ int radix_sort_pairs(int32_t *keys, int32_t *vals, int32_t *tmp_k, int32_t *tmp_
   return LAGR_OK;
 }
 
-int heavy_rows(const int32_t *rowptr, int32_t n, int32_t threshold, int32_t **list, int32_t *count, cudaStream_t s,
-               char *msg) {
-  *list = nullptr;
-  *count = 0;
-  if (n <= 0) return LAGR_OK;
-  Temp<int32_t> flag(s), pos(s);
-  LAGR_TRY(flag.alloc(n, msg, "heavy flags"));
-  LAGR_TRY(pos.alloc((size_t)n + 1, msg, "heavy positions"));
-  mark_heavy<<<grid_for(n, 256), 256, 0, s>>>(rowptr, n, threshold, flag.p);
-  LAGR_TRY(exclusive_scan(flag.p, pos.p, n, s, msg));
-  int32_t h = 0;
-  LAGR_CUDA_TRY(cudaMemcpyAsync(&h, pos.p + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
-  int32_t *l = nullptr;
-  LAGR_TRY(alloc_n(&l, (size_t)h + 1, s, msg, "heavy row list"));
-  if (h > 0) scatter_heavy<<<grid_for(n, 256), 256, 0, s>>>(flag.p, pos.p, n, l);
-  LAGR_LAUNCH_CHECK();
-  *list = l;
-  *count = h;
-  return LAGR_OK;
-}
-
 int transpose_csr(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx, const float *val,
                   int32_t *at_rowptr, int32_t *at_colidx, float *at_val, cudaStream_t s, char *msg) {
   Temp<int32_t> cnt(s);
@@ -354,114 +362,83 @@ int transpose_csr(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *
   return LAGR_OK;
 }
 
-// Build (once) the row plan of a CSR: heavy rows and row blocks.  Synchronises the stream.
+// Build (once) the row plan of a CSR: heavy rows and row blocks.  Every step runs on the device;
+// the host reads four counts (two synchronisations).
 int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char *msg, int32_t units, int32_t hv,
              int32_t hchunk) {
   if (pl->nblk >= 0) return LAGR_OK;
-  int32_t *heavy = nullptr, nheavy = 0;
-  LAGR_TRY(heavy_rows(rowptr, n, hv, &heavy, &nheavy, s, msg));
-  Temp<int32_t> ld(s), lp(s);
-  int st = ld.alloc(n, msg, "light degrees");
-  if (st == LAGR_OK) st = lp.alloc((size_t)n + 1, msg, "light prefix");
-  if (st < 0) {
-    dev_free(heavy, s);
-    return st;
-  }
-  light_degree<<<grid_for(n, 256), 256, 0, s>>>(rowptr, n, hv, ld.p);
-  st = exclusive_scan(ld.p, lp.p, n, s, msg);
-  int32_t light = 0;
-  cudaError_t e = cudaGetLastError();
-  if (st == LAGR_OK && e == cudaSuccess) e = cudaMemcpyAsync(&light, lp.p + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if (st == LAGR_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (st == LAGR_OK && e != cudaSuccess) {
-    set_msg(msg, "row plan: %s", cudaGetErrorString(e));
-    st = LAGR_ERR_CUDA;
-  }
-  // block starts: the first row at or after every ROW_UNITS-th unit, plus each heavy row and the
-  // row after it, so that every heavy row is a block of its own (merged on the host, once)
-  const int64_t nb0 = ((int64_t)light + n) / units + 1;
-  int32_t *blk = nullptr;
+  int32_t *heavy = nullptr, *blk = nullptr, *hc_off = nullptr, *hc_row = nullptr;
   uint8_t *hblk = nullptr;
-  int64_t nblk = 0;
+  int32_t nheavy = 0, nblk = 0, nhc = 0;
+  int st = LAGR_OK;
   {
-    Temp<int32_t> b0(s);
+    Temp<int32_t> hflag(s), hpos(s), ld(s), lp(s), b0(s), mark(s), mpos(s), nch(s);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    st = hflag.alloc(nn, msg, "heavy flags");
+    if (st == LAGR_OK) st = hpos.alloc((size_t)n + 1, msg, "heavy positions");
+    if (st == LAGR_OK) st = ld.alloc(nn, msg, "light degrees");
+    if (st == LAGR_OK) st = lp.alloc((size_t)n + 1, msg, "light prefix");
+    if (st == LAGR_OK) {
+      row_classes<<<grid_for(n, 256), 256, 0, s>>>(rowptr, n, hv, hflag.p, ld.p);
+      st = exclusive_scan(hflag.p, hpos.p, n, s, msg);
+    }
+    if (st == LAGR_OK) st = exclusive_scan(ld.p, lp.p, n, s, msg);
+    int32_t light = 0;
+    if (st == LAGR_OK) {
+      const int32_t *src[2] = {hpos.p + n, lp.p + n};
+      int32_t got[2];
+      st = fetch_i32s(got, src, 2, s, msg);
+      nheavy = got[0];
+      light = got[1];
+    }
+    if (st == LAGR_OK) st = alloc_n(&heavy, (size_t)nheavy + 1, s, msg, "heavy row list");
+    if (st == LAGR_OK && nheavy > 0) scatter_heavy<<<grid_for(n, 256), 256, 0, s>>>(hflag.p, hpos.p, n, heavy);
+    // block starts: the first row at or after every units-th unit, plus each heavy row and the row
+    // after it, so that every heavy row is a block of its own; marked per row, compacted by a scan
+    const int64_t nb0 = ((int64_t)light + n) / units + 1;
+    const int64_t ub64 = std::max<int64_t>(1, std::min<int64_t>(n, nb0 + 2 * (int64_t)nheavy));
     if (st == LAGR_OK) st = b0.alloc((size_t)nb0 + 1, msg, "row block starts");
+    if (st == LAGR_OK) st = mark.alloc(nn, msg, "block marks");
+    if (st == LAGR_OK) st = mpos.alloc((size_t)n + 1, msg, "block positions");
+    if (st == LAGR_OK) st = alloc_n(&blk, (size_t)ub64 + 1, s, msg, "row blocks");
+    if (st == LAGR_OK) st = alloc_n(&hblk, (size_t)ub64, s, msg, "heavy block flags");
     if (st == LAGR_OK) {
       block_starts<<<grid_for(nb0 + 1, 256), 256, 0, s>>>(lp.p, n, (int32_t)nb0, units, b0.p);
-      e = cudaGetLastError();
-    }
-    std::vector<int32_t> hb((size_t)nb0 + 1), hh((size_t)nheavy);
-    if (st == LAGR_OK && e == cudaSuccess)
-      e = cudaMemcpyAsync(hb.data(), b0.p, hb.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (st == LAGR_OK && e == cudaSuccess && nheavy > 0)
-      e = cudaMemcpyAsync(hh.data(), heavy, hh.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (st == LAGR_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (st == LAGR_OK && e != cudaSuccess) {
-      set_msg(msg, "row plan: %s", cudaGetErrorString(e));
-      st = LAGR_ERR_CUDA;
-    }
-    if (st == LAGR_OK) {
-      std::vector<int32_t> hcut;  // heavy rows and the rows after them (ascending)
-      hcut.reserve(2 * hh.size());
-      for (int32_t h : hh) {
-        if (hcut.empty() || hcut.back() != h) hcut.push_back(h);
-        hcut.push_back(h + 1);
-      }
-      std::vector<int32_t> cut;  // every block start, then n
-      cut.reserve(hb.size() + hcut.size());
-      std::merge(hb.begin(), hb.end() - 1, hcut.begin(), hcut.end(), std::back_inserter(cut));
-      cut.erase(std::unique(cut.begin(), cut.end()), cut.end());
-      while (!cut.empty() && cut.back() >= n) cut.pop_back();
-      if (cut.empty() || cut.front() != 0) cut.insert(cut.begin(), 0);
-      nblk = (int64_t)cut.size();
-      cut.push_back(n);
-      std::vector<uint8_t> flag((size_t)nblk, 0);
-      size_t q = 0;
-      for (int64_t b = 0; b < nblk && q < hh.size(); b++) {
-        while (q < hh.size() && hh[q] < cut[b]) q++;
-        if (q < hh.size() && hh[q] == cut[b] && cut[b + 1] == cut[b] + 1) flag[b] = 1;
-      }
-      st = alloc_n(&blk, (size_t)nblk + 1, s, msg, "row blocks");
-      if (st == LAGR_OK) st = alloc_n(&hblk, (size_t)nblk, s, msg, "heavy block flags");
-      if (st == LAGR_OK) e = cudaMemcpyAsync(blk, cut.data(), cut.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-      if (st == LAGR_OK && e == cudaSuccess)
-        e = cudaMemcpyAsync(hblk, flag.data(), flag.size(), cudaMemcpyHostToDevice, s);
-      // the host vectors must outlive the copies
-      if (st == LAGR_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (st == LAGR_OK && e != cudaSuccess) {
-        set_msg(msg, "row plan: %s", cudaGetErrorString(e));
-        st = LAGR_ERR_CUDA;
-      }
-    }
-  }
-  if (st < 0) {
-    dev_free(heavy, s);
-    dev_free(blk, s);
-    dev_free(hblk, s);
-    return st;
-  }
-  // chunks of the heavy rows
-  int32_t *hc_off = nullptr, *hc_row = nullptr, nhc = 0;
-  if (st == LAGR_OK && nheavy > 0) {
-    Temp<int32_t> nch(s);
-    st = nch.alloc(nheavy, msg, "heavy chunk counts");
-    if (st == LAGR_OK) st = alloc_n(&hc_off, (size_t)nheavy + 1, s, msg, "heavy chunk offsets");
-    if (st == LAGR_OK) {
-      heavy_chunk_counts<<<grid_for(nheavy, 256), 256, 0, s>>>(rowptr, heavy, nheavy, hchunk, nch.p);
-      st = exclusive_scan(nch.p, hc_off, nheavy, s, msg);
-    }
-    if (st == LAGR_OK) {
-      e = cudaMemcpyAsync(&nhc, hc_off + nheavy, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      const cudaError_t e = cudaMemsetAsync(mark.p, 0, nn * sizeof(int32_t), s);
       if (e != cudaSuccess) {
         set_msg(msg, "row plan: %s", cudaGetErrorString(e));
         st = LAGR_ERR_CUDA;
       }
     }
-    if (st == LAGR_OK) st = alloc_n(&hc_row, (size_t)nhc, s, msg, "heavy chunk rows");
     if (st == LAGR_OK) {
-      heavy_chunk_rows<<<grid_for(nheavy, 256), 256, 0, s>>>(hc_off, nheavy, hc_row);
-      e = cudaGetLastError();
+      mark_cuts<<<grid_for(std::max<int64_t>(nb0, nheavy), 256), 256, 0, s>>>(b0.p, (int32_t)nb0, heavy, nheavy, n,
+                                                                              mark.p);
+      st = exclusive_scan(mark.p, mpos.p, n, s, msg);
+    }
+    if (st == LAGR_OK)
+      scatter_blocks<<<grid_for(n, 256), 256, 0, s>>>(mark.p, mpos.p, rowptr, n, hv, blk, hblk);
+    // chunks of the heavy rows
+    if (st == LAGR_OK && nheavy > 0) {
+      st = nch.alloc(nheavy, msg, "heavy chunk counts");
+      if (st == LAGR_OK) st = alloc_n(&hc_off, (size_t)nheavy + 1, s, msg, "heavy chunk offsets");
+      if (st == LAGR_OK) {
+        heavy_chunk_counts<<<grid_for(nheavy, 256), 256, 0, s>>>(rowptr, heavy, nheavy, hchunk, nch.p);
+        st = exclusive_scan(nch.p, hc_off, nheavy, s, msg);
+      }
+    }
+    if (st == LAGR_OK) {
+      const int32_t *src[2] = {mpos.p + n, nheavy > 0 ? hc_off + nheavy : mpos.p + n};
+      int32_t got[2];
+      st = fetch_i32s(got, src, 2, s, msg);
+      nblk = n > 0 ? got[0] : 1;
+      nhc = nheavy > 0 ? got[1] : 0;
+    }
+    if (st == LAGR_OK && nheavy > 0) {
+      st = alloc_n(&hc_row, (size_t)(nhc > 0 ? nhc : 1), s, msg, "heavy chunk rows");
+      if (st == LAGR_OK) heavy_chunk_rows<<<grid_for(nheavy, 256), 256, 0, s>>>(hc_off, nheavy, hc_row);
+    }
+    if (st == LAGR_OK) {
+      const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         set_msg(msg, "row plan: %s", cudaGetErrorString(e));
         st = LAGR_ERR_CUDA;
@@ -479,7 +456,7 @@ int row_plan(RowPlan *pl, const int32_t *rowptr, int32_t n, cudaStream_t s, char
   pl->heavy = heavy;
   pl->nheavy = nheavy;
   pl->blk = blk;
-  pl->nblk = (int32_t)nblk;
+  pl->nblk = nblk;
   pl->hc_off = hc_off;
   pl->hc_row = hc_row;
   pl->nhc = nhc;

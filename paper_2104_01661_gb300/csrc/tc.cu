@@ -53,6 +53,8 @@ constexpr int SL_QC = SC_COUNT6;
 constexpr int SL_TOTAL = SC_COUNT7;
 constexpr int SL_QWL = SC_COUNT8;  // queue cursor of the whole-anchor warp items
 constexpr int SL_NWF = SC_COUNT9;  // heavier warp anchors (one item each), stored from the front of listw
+constexpr int SL_NSW = SC_COUNT10;  // U rows listed for the warp sorter
+constexpr int SL_NSC = SC_COUNT11;  // U rows listed for the CTA sorter
 
 __device__ __forceinline__ uint32_t hslot(int32_t w, int logT) {
   return ((uint32_t)w * 0x9E3779B1u) >> (32 - logT);
@@ -272,6 +274,132 @@ __global__ void tc_orient_heavy(const int32_t *__restrict__ rowptr, const int32_
   }
 }
 
+// ---- U rows in descending rank order ------------------------------------------------------------
+//
+// A probe list of at least 32 entries is walked by a whole warp (anchor_batch), and such a walk can
+// stop at the list's first entry ranked at or below the anchor if the list is in descending rank
+// order: no later entry can be in the anchor's list.  So every U row of 32 .. TC_SORT_MAX entries
+// is sorted (bitonic networks in shared memory: by a warp up to TC_SORT_WARP entries, by a CTA
+// above); shorter rows are probed entry by entry anyway, and longer rows keep their order and are
+// walked to the end.  The rows to sort are listed first, then taken from queues.
+constexpr int TC_SORT_MIN = 32;
+constexpr int TC_SORT_WARP = 2048;
+constexpr int TC_SORT_MAX = 16384;
+constexpr int TCS_WARPS = 4;  // warps per CTA of the warp sorter
+
+__global__ void tc_sort_collect(const int32_t *__restrict__ dplus, int32_t n, int32_t *__restrict__ listw,
+                                int32_t *__restrict__ listc, int64_t *__restrict__ dscal) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t v = base + lane;
+    const int32_t d = v < n ? dplus[v] : 0;
+    const bool w = d >= TC_SORT_MIN && d <= TC_SORT_WARP, c = d > TC_SORT_WARP && d <= TC_SORT_MAX;
+    const unsigned bw = __ballot_sync(LAGR_FULL_MASK, w), bc = __ballot_sync(LAGR_FULL_MASK, c);
+    unsigned long long pw = 0, pc = 0;
+    if (lane == 0 && bw) pw = atomicAdd((unsigned long long *)&dscal[SL_NSW], (unsigned long long)__popc(bw));
+    if (lane == 0 && bc) pc = atomicAdd((unsigned long long *)&dscal[SL_NSC], (unsigned long long)__popc(bc));
+    pw = __shfl_sync(LAGR_FULL_MASK, pw, 0);
+    pc = __shfl_sync(LAGR_FULL_MASK, pc, 0);
+    if (w) listw[pw + __popc(bw & lt)] = (int32_t)v;
+    if (c) listc[pc + __popc(bc & lt)] = (int32_t)v;
+  }
+}
+
+__device__ __forceinline__ void cmpx_desc(int32_t *s, int32_t i, int32_t ixj, bool desc) {
+  const int32_t a = s[i], b = s[ixj];
+  if ((a < b) == desc) {
+    s[i] = b;
+    s[ixj] = a;
+  }
+}
+
+// one compare-exchange of a bitonic stage between lanes lane and lane ^ j (j < 32): in a descending
+// segment the lower index keeps the larger value
+__device__ __forceinline__ int32_t shfl_cmpx(int32_t x, int j, bool desc, int lane) {
+  const int32_t y = __shfl_xor_sync(LAGR_FULL_MASK, x, j);
+  return (((lane & j) == 0) == desc) ? max(x, y) : min(x, y);
+}
+
+// Bitonic sort of one row by one warp.  Element i sits in lane i % 32 for the stages whose partner
+// distance j is below 32 (shuffles, each element loaded once per merge size k), in shared memory for
+// the others (j >= 32: lane l handles pair l, l + 32, ... with both ends active).
+__global__ void __launch_bounds__(TCS_WARPS * 32)
+    tc_sort_rows_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus,
+                      const int32_t *__restrict__ list, const int64_t *__restrict__ dscal,
+                      int32_t *__restrict__ u_colidx) {
+  __shared__ int32_t buf[TCS_WARPS][TC_SORT_WARP];
+  const int lane = threadIdx.x & 31;
+  int32_t *sb = buf[threadIdx.x >> 5];
+  const int64_t nl = dscal[SL_NSW];
+  const int64_t nw = (int64_t)gridDim.x * TCS_WARPS;
+  for (int64_t it = (int64_t)blockIdx.x * TCS_WARPS + (threadIdx.x >> 5); it < nl; it += nw) {
+    const int32_t v = list[it];
+    const int32_t d = dplus[v];
+    int32_t *row = u_colidx + rowptr[v];
+    int32_t P = TC_SORT_MIN;
+    while (P < d) P <<= 1;
+    // merge sizes 2 .. 32: each 32-element group sorted in registers, alternating direction
+    for (int32_t i = lane; i < P; i += 32) {
+      int32_t x = i < d ? row[i] : INT32_MIN;
+#pragma unroll
+      for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) x = shfl_cmpx(x, j, (i & k) == 0, lane);
+      sb[i] = x;
+    }
+    __syncwarp();
+    for (int32_t k = 64; k <= P; k <<= 1) {
+      for (int32_t j = k >> 1; j >= 32; j >>= 1) {
+        for (int32_t q = lane; q < (P >> 1); q += 32) {
+          const int32_t i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+          cmpx_desc(sb, i, i + j, (i & k) == 0);
+        }
+        __syncwarp();
+      }
+      for (int32_t i = lane; i < P; i += 32) {
+        int32_t x = sb[i];
+#pragma unroll
+        for (int j = 16; j > 0; j >>= 1) x = shfl_cmpx(x, j, (i & k) == 0, lane);
+        sb[i] = x;
+      }
+      __syncwarp();
+    }
+    for (int32_t i = lane; i < d; i += 32) row[i] = sb[i];
+    __syncwarp();
+  }
+}
+
+// the rows of TC_SORT_WARP < d+ <= TC_SORT_MAX: one CTA each (dynamic shared memory TC_SORT_MAX ints)
+constexpr int TCS_CTA_THREADS = 1024;
+__global__ void __launch_bounds__(TCS_CTA_THREADS)
+    tc_sort_rows_cta(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus,
+                     const int32_t *__restrict__ list, const int64_t *__restrict__ dscal,
+                     int32_t *__restrict__ u_colidx) {
+  extern __shared__ int32_t sbig[];
+  const int64_t nl = dscal[SL_NSC];
+  for (int64_t it = blockIdx.x; it < nl; it += gridDim.x) {
+    const int32_t v = list[it];
+    const int32_t d = dplus[v];
+    int32_t *row = u_colidx + rowptr[v];
+    int32_t P = TC_SORT_WARP * 2;
+    while (P < d) P <<= 1;
+    for (int32_t i = threadIdx.x; i < P; i += blockDim.x) sbig[i] = i < d ? row[i] : INT32_MIN;
+    __syncthreads();
+    for (int32_t k = 2; k <= P; k <<= 1)
+      for (int32_t j = k >> 1; j > 0; j >>= 1) {
+        for (int32_t i = threadIdx.x; i < P; i += blockDim.x) {
+          const int32_t ixj = i ^ j;
+          if (ixj > i) cmpx_desc(sbig, i, ixj, (i & k) == 0);
+        }
+        __syncthreads();
+      }
+    for (int32_t i = threadIdx.x; i < d; i += blockDim.x) row[i] = sbig[i];
+    __syncthreads();
+  }
+}
+
 // ---- anchors: warp class (short list, moderate degree) and CTA items -------------------------------
 
 __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus, int32_t n,
@@ -337,7 +465,7 @@ __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *_
 // (smaller (d+, id)), probe each element of U(y,:) = u_colidx[ustart[y] .. ustart[y] + dplus[y])
 // against x's set.  Warp-collective.
 template <class Probe>
-__device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a, int32_t jb, int32_t e,
+__device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a, int32_t rx, int32_t jb, int32_t e,
                                                            const int32_t *__restrict__ colidx,
                                                            const int32_t *__restrict__ ustart,
                                                            const int32_t *__restrict__ u_colidx,
@@ -379,12 +507,24 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
     longs &= longs - 1;
     const int32_t *lst = u_colidx + __shfl_sync(LAGR_FULL_MASK, st, sl);
     const int32_t len_s = __shfl_sync(LAGR_FULL_MASK, len, sl);
-    int32_t k = lane;
-    for (; k + 96 < len_s; k += 128) {  // four loads per lane in flight
+    // a sorted list (descending ranks) ends its useful part at its first entry <= rx
+    const bool sorted = len_s >= TC_SORT_MIN && len_s <= TC_SORT_MAX;
+    int32_t base = 0;  // warp-uniform: every lane runs every round
+    for (; base + 128 <= len_s; base += 128) {  // four loads per lane in flight
+      const int32_t k = base + lane;
       const int32_t w0 = lst[k], w1 = lst[k + 32], w2 = lst[k + 64], w3 = lst[k + 96];
       c += (probe(w0) + probe(w1)) + (probe(w2) + probe(w3));
+      if (sorted && __shfl_sync(LAGR_FULL_MASK, w3, 31) <= rx) {  // the round's last position
+        base = len_s;
+        break;
+      }
     }
-    for (; k < len_s; k += 32) c += probe(lst[k]);
+    for (; base < len_s; base += 32) {
+      const int32_t k = base + lane;
+      const int32_t w = k < len_s ? lst[k] : 0;
+      if (k < len_s) c += probe(w);
+      if (sorted && __shfl_sync(LAGR_FULL_MASK, w, min(31, len_s - 1 - base)) <= rx) break;
+    }
   }
   return c;
 }
@@ -450,7 +590,7 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
     __syncwarp();
     unsigned long long c = 0;
     for (int32_t jb = jb0; jb < je; jb += 32)
-      c += anchor_batch(x, a, jb, je, colidx, ustart, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
+      c += anchor_batch(x, a, rs.rx, jb, je, colidx, ustart, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
     __syncwarp();
     for (int i = lane; i < a; i += 32) rs.erase(u_colidx[ub + i]);
     if (voff) {
@@ -523,7 +663,7 @@ __global__ void __launch_bounds__(TCC_THREADS)
       if (lane == 0) jb = atomicAdd(&s_next, 32);
       jb = __shfl_sync(LAGR_FULL_MASK, jb, 0);
       if (jb >= e) break;
-      c += anchor_batch(x, a, jb, e, colidx, ustart, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
+      c += anchor_batch(x, a, rs.rx, jb, e, colidx, ustart, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
     }
     if (voff) {
       c = warp_sum(c);
@@ -606,6 +746,10 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
               unsigned long long *counts, bool orient, cudaStream_t s, char *msg) {
   const int32_t n = G->n;
   const int64_t nnz = G->nnz;
+  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_sort_rows_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(TC_SORT_MAX * sizeof(int32_t))));
+  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCC_SMEM));
+  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCW_SMEM));
   if (orient) {
     LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal, 0, LAGR_NSCAL * sizeof(int64_t), s));
     if (method == LAGR_TC_AUTO) {
@@ -626,6 +770,13 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
     if (rp.nheavy > 0)
       tc_orient_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, G->u_dplus, G->u_colidx, rp.heavy,
                                               rp.nheavy);
+    {  // the rows to sort are listed in the rank-sort buffers (free again once the ranks are made)
+      int32_t *lw = P->tc_sortbuf, *lc = P->tc_sortbuf + n;
+      tc_sort_collect<<<grid_for(n, 256), 256, 0, s>>>(G->u_dplus, n, lw, lc, P->dscal);
+      tc_sort_rows_warp<<<152 * 8, TCS_WARPS * 32, 0, s>>>(G->rowptr, G->u_dplus, lw, P->dscal, G->u_colidx);
+      tc_sort_rows_cta<<<152, TCS_CTA_THREADS, TC_SORT_MAX * sizeof(int32_t), s>>>(G->rowptr, G->u_dplus, lc,
+                                                                                    P->dscal, G->u_colidx);
+    }
     tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, P->tc_listw, P->tc_listwh,
                                                  P->tc_capwh, P->tc_listc, P->tc_capc, P->dscal, prm.wmax,
                                                  prm.chunk);
@@ -637,8 +788,6 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
   }
   if (counts != (unsigned long long *)(P->dscal + SL_TOTAL))
     LAGR_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ngraphs * sizeof(unsigned long long), s));
-  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCC_SMEM));
-  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCW_SMEM));
   // windows: the top ranks [n - window, n) (or all of them on small graphs)
   const int32_t w0c = n > (1 << TCC_WIN_LOG) ? n - (1 << TCC_WIN_LOG) : 0;
   const int32_t w0w = n > (1 << TCW_WIN_LOG) ? n - (1 << TCW_WIN_LOG) : 0;
@@ -692,8 +841,7 @@ extern "C" int lagr_tc(uint64_t *ntriangles, lagr_graph G, int32_t method, void 
   LAGR_TRY(tc_alloc(G, P, prm, s, msg));
   LAGR_TRY(tc_launch(G, P, method, prm, nullptr, 1, tc_total_slot(P), !cached, s, msg));
   G->u_order = method;
-  LAGR_CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, LAGR_NSCAL * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+  LAGR_TRY(fetch_to_host(P->hscal, P->dscal, LAGR_NSCAL * sizeof(int64_t), s, msg));
   if (P->hscal[SC_ERR] != 0) {
     set_msg(msg, "oriented graph overflowed: the undirected graph is not symmetric");
     return LAGR_ERR_INVALID_GRAPH;

@@ -148,3 +148,10 @@ def test_timing_api_host_side(lib):
         assert lib.lagr_timing_read(name, ctypes.byref(ms), ctypes.byref(cnt)) == 0
         assert ms.value == 0.0 and cnt.value == 0
     assert lib.lagr_timing_enable(1) == 0 and lib.lagr_timing_enable(0) == 0
+
+
+def test_release_memory_without_pools(lib):
+    msg = ctypes.create_string_buffer(L.LAGR_MSG_LEN)
+    msg.value = b"stale"
+    assert lib.lagr_release_memory(0, msg) == 0 and msg.value == b""
+    assert lib.lagr_release_memory(1 << 40, None) == 0

@@ -512,3 +512,34 @@ def test_kernel_timing_counts_launches(L, rmat12):
     L.timing_reset()
     L.lagr_pagerank(G, 0.85, 0.0, 3)
     assert L.timing_read("pr_gather") == (0.0, 0)
+
+
+@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("n", [3000, 10000, 20000])
+def test_tc_sorted_and_unsorted_probe_lists(L, method, n):
+    # two hubs joined to each other and to every other vertex: n - 2 triangles.  Without the degree
+    # order (NOSORT) the second hub's list U(1) = {2..n-1} is a long probe list: sorted by a whole
+    # CTA at n = 3000 and 10000, longer than the rows that are kept sorted at n = 20000 (its probe
+    # walk must then run to the end); with the degree order the lists are short.
+    v = np.arange(2, n, dtype=np.int64)
+    src = np.concatenate([[0], np.zeros_like(v), np.ones_like(v)])
+    dst = np.concatenate([[1], v, v])
+    g = gen.from_edges(n, src, dst)
+    G = dev(L, g)
+    assert L.lagr_tc(G, method) == n - 2
+    # plus a cycle through the leaves: each cycle edge (v, v+1) closes two more triangles
+    src2 = np.concatenate([src, v[:-1]])
+    dst2 = np.concatenate([dst, v[1:]])
+    g2 = gen.from_edges(n, src2, dst2)
+    assert L.lagr_tc(dev(L, g2), method) == (n - 2) + 2 * (n - 3) == oracle.tc(g2)
+
+
+def test_release_memory_between_graphs(L, rmat12):
+    # graphs freed, their pooled memory trimmed, then a new graph allocates again from the pool
+    t = oracle.tc(rmat12)
+    for keep in (0, 1 << 30):
+        G = dev(L, rmat12)
+        assert L.lagr_tc(G) == t
+        G.free()
+        L.lagr_release_memory(keep)
+    assert L.lagr_tc(dev(L, rmat12)) == t
