@@ -223,7 +223,8 @@ def run_gpu(args):
     # End to end through the public API with host buffers: every step copies its CSR from pinned
     # host memory and its results (all levels, parents and ranks) back.  The copies run on a second
     # stream, pipelined with the compute: the next step's CSR is uploaded and the previous step's
-    # results (double-buffered) are downloaded while a step computes.
+    # results are downloaded while a step computes (inputs and outputs double-buffered on the
+    # device, so the timed loop allocates nothing).
     h2d = rp_h.numel() * 4 + ci_h.numel() * 4
     outs = [(level, parent, rank_v),
             (torch.empty_like(level), torch.empty_like(parent), torch.empty_like(rank_v))]
@@ -234,37 +235,49 @@ def run_gpu(args):
     copy = torch.cuda.Stream(dev)
 
     up_marks, down_marks = [], []  # copy-stream events around every upload and download
+    # the device CSR buffers the uploads fill (two, reused: no allocation inside the timed loop)
+    dev_in = [(torch.empty_like(rp), torch.empty_like(ci)) for _ in range(2)]
+    consumed = [None, None]  # per input buffer: the end of the last step that read it
 
-    def upload():
+    def upload(k):
+        rp_d, ci_d = dev_in[k % 2]
         with torch.cuda.stream(copy):
+            if consumed[k % 2] is not None:
+                copy.wait_event(consumed[k % 2])
             a, b = ev(), ev()
             a.record(copy)
-            rp_d = rp_h.to(dev, non_blocking=True)
-            ci_d = ci_h.to(dev, non_blocking=True)
+            rp_d.copy_(rp_h, non_blocking=True)
+            ci_d.copy_(ci_h, non_blocking=True)
             ready = torch.cuda.Event()
             ready.record(copy)
             b.record(copy)
             up_marks.append((a, b))
-        return rp_d, ci_d, ready
+        return ready
+
+    # warm the copy path once (first-use costs of the copy stream and the pinned buffers)
+    upload(0)
+    for h, d in zip(hosts[0], outs[0]):
+        h.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    up_marks.clear()
 
     e_start, e_end = ev(), ev()
-    torch.cuda.synchronize()
     e_start.record(stream)
     copy.wait_event(e_start)
-    nxt = upload()
+    ready = upload(0)
     freed = [None, None]  # per output buffer: the download of its previous contents
+    e_marks = []  # per step: the component boundaries, as in the device-timed loop
     for k in range(args.steps):
-        rp_d, ci_d, ready = nxt
         stream.wait_event(ready)
-        rp_d.record_stream(stream)
-        ci_d.record_stream(stream)
         if k + 1 < args.steps:
-            nxt = upload()
+            ready_next = upload(k + 1)
         if freed[k % 2] is not None:
             stream.wait_event(freed[k % 2])
-        step(rp_d, ci_d, out=outs[k % 2])
+        e_marks.append([ev() for _ in range(4)])
+        step(dev_in[k % 2][0], dev_in[k % 2][1], e_marks[-1], out=outs[k % 2])
         done = torch.cuda.Event()
         done.record(stream)
+        consumed[k % 2] = done
         with torch.cuda.stream(copy):
             copy.wait_event(done)
             a, b = ev(), ev()
@@ -275,12 +288,16 @@ def run_gpu(args):
             down_marks.append((a, b))
             freed[k % 2] = torch.cuda.Event()
             freed[k % 2].record(copy)
+        if k + 1 < args.steps:
+            ready = ready_next
     for f in freed:
         if f is not None:
             stream.wait_event(f)
     e_end.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), world) / args.steps
+    e_parts = [statistics.median(m[i].elapsed_time(m[i + 1]) for m in e_marks) if e_marks else 0.0
+               for i in range(3)]
     up_ms = statistics.median(a.elapsed_time(b) for a, b in up_marks) if up_marks else 0.0
     down_ms = statistics.median(a.elapsed_time(b) for a, b in down_marks) if down_marks else 0.0
     if args.steps > 0 and only in ("all", "bfs"):  # the downloaded levels are the computed ones
@@ -319,7 +336,8 @@ def run_gpu(args):
             "clocks": clocks,
             "e2e": {"value": round(job_throughput(edges_per_step, world, e2e_ms) / 1e9, 4), "unit": "GTEPS",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": round(e2e_ms, 3), "h2d_ms": round(up_ms, 3), "d2h_ms": round(down_ms, 3)},
+                    "ms_per_step": round(e2e_ms, 3), "h2d_ms": round(up_ms, 3), "d2h_ms": round(down_ms, 3),
+                    "tc_ms": round(e_parts[0], 3), "bfs_ms": round(e_parts[1], 3), "pr_ms": round(e_parts[2], 3)},
             "gpu_launches": launches_timed,
             "components": {
                 "triangles": t_tri, "tc_ms": round(tc_ms, 3),

@@ -279,11 +279,11 @@ __global__ void tc_orient_heavy(const int32_t *__restrict__ rowptr, const int32_
 // A probe list of at least 32 entries is walked by a whole warp (anchor_batch), and such a walk can
 // stop at the list's first entry ranked at or below the anchor if the list is in descending rank
 // order: no later entry can be in the anchor's list.  So every U row of 32 .. TC_SORT_MAX entries
-// is sorted (bitonic networks in shared memory: by a warp up to TC_SORT_WARP entries, by a CTA
-// above); shorter rows are probed entry by entry anyway, and longer rows keep their order and are
-// walked to the end.  The rows to sort are listed first, then taken from queues.
+// is sorted (bitonic networks: by a warp in registers up to TC_SORT_WARP entries, by a CTA in
+// shared memory above); shorter rows are probed entry by entry anyway, and longer rows keep their
+// order and are walked to the end.  The rows to sort are listed first.
 constexpr int TC_SORT_MIN = 32;
-constexpr int TC_SORT_WARP = 2048;
+constexpr int TC_SORT_WARP = 1024;
 constexpr int TC_SORT_MAX = 16384;
 constexpr int TCS_WARPS = 4;  // warps per CTA of the warp sorter
 
@@ -322,52 +322,64 @@ __device__ __forceinline__ int32_t shfl_cmpx(int32_t x, int j, bool desc, int la
   return (((lane & j) == 0) == desc) ? max(x, y) : min(x, y);
 }
 
-// Bitonic sort of one row by one warp.  Element i sits in lane i % 32 for the stages whose partner
-// distance j is below 32 (shuffles, each element loaded once per merge size k), in shared memory for
-// the others (j >= 32: lane l handles pair l, l + 32, ... with both ends active).
+// Bitonic sort of one row of at most P entries by one warp, entirely in registers: element i sits in
+// lane i % 32, register i / 32.  A stage of partner distance j >= 32 pairs registers of the same lane;
+// below 32 it pairs lanes (shuffles).  The direction of every pair is fixed by the unrolled loops
+// except in the stages with merge size k <= 16.
+template <int P>
+__device__ __forceinline__ void warp_sort_desc(int32_t *__restrict__ row, int32_t d, int lane) {
+  constexpr int R = P / 32;
+  int32_t v[R];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int32_t i = lane + 32 * r;
+    v[r] = i < d ? row[i] : INT32_MIN;
+  }
+#pragma unroll
+  for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int jr = j >> 5;
+#pragma unroll
+        for (int r = 0; r < R; r++)
+          if ((r & jr) == 0) {
+            const bool desc = ((32 * r) & k) == 0;
+            const int32_t a = v[r], b = v[r | jr];
+            v[r] = desc ? max(a, b) : min(a, b);
+            v[r | jr] = desc ? min(a, b) : max(a, b);
+          }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = shfl_cmpx(v[r], j, ((lane + 32 * r) & k) == 0, lane);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const int32_t i = lane + 32 * r;
+    if (i < d) row[i] = v[r];
+  }
+}
+
+// the rows of TC_SORT_MIN <= d+ <= TC_SORT_WARP: one warp each, in registers
 __global__ void __launch_bounds__(TCS_WARPS * 32)
     tc_sort_rows_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus,
                       const int32_t *__restrict__ list, const int64_t *__restrict__ dscal,
                       int32_t *__restrict__ u_colidx) {
-  __shared__ int32_t buf[TCS_WARPS][TC_SORT_WARP];
   const int lane = threadIdx.x & 31;
-  int32_t *sb = buf[threadIdx.x >> 5];
   const int64_t nl = dscal[SL_NSW];
   const int64_t nw = (int64_t)gridDim.x * TCS_WARPS;
   for (int64_t it = (int64_t)blockIdx.x * TCS_WARPS + (threadIdx.x >> 5); it < nl; it += nw) {
     const int32_t v = list[it];
     const int32_t d = dplus[v];
     int32_t *row = u_colidx + rowptr[v];
-    int32_t P = TC_SORT_MIN;
-    while (P < d) P <<= 1;
-    // merge sizes 2 .. 32: each 32-element group sorted in registers, alternating direction
-    for (int32_t i = lane; i < P; i += 32) {
-      int32_t x = i < d ? row[i] : INT32_MIN;
-#pragma unroll
-      for (int k = 2; k <= 32; k <<= 1)
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) x = shfl_cmpx(x, j, (i & k) == 0, lane);
-      sb[i] = x;
-    }
-    __syncwarp();
-    for (int32_t k = 64; k <= P; k <<= 1) {
-      for (int32_t j = k >> 1; j >= 32; j >>= 1) {
-        for (int32_t q = lane; q < (P >> 1); q += 32) {
-          const int32_t i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
-          cmpx_desc(sb, i, i + j, (i & k) == 0);
-        }
-        __syncwarp();
-      }
-      for (int32_t i = lane; i < P; i += 32) {
-        int32_t x = sb[i];
-#pragma unroll
-        for (int j = 16; j > 0; j >>= 1) x = shfl_cmpx(x, j, (i & k) == 0, lane);
-        sb[i] = x;
-      }
-      __syncwarp();
-    }
-    for (int32_t i = lane; i < d; i += 32) row[i] = sb[i];
-    __syncwarp();
+    if (d <= 32) warp_sort_desc<32>(row, d, lane);
+    else if (d <= 64) warp_sort_desc<64>(row, d, lane);
+    else if (d <= 128) warp_sort_desc<128>(row, d, lane);
+    else if (d <= 256) warp_sort_desc<256>(row, d, lane);
+    else if (d <= 512) warp_sort_desc<512>(row, d, lane);
+    else warp_sort_desc<TC_SORT_WARP>(row, d, lane);
   }
 }
 
@@ -510,13 +522,26 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
     // a sorted list (descending ranks) ends its useful part at its first entry <= rx
     const bool sorted = len_s >= TC_SORT_MIN && len_s <= TC_SORT_MAX;
     int32_t base = 0;  // warp-uniform: every lane runs every round
-    for (; base + 128 <= len_s; base += 128) {  // four loads per lane in flight
-      const int32_t k = base + lane;
-      const int32_t w0 = lst[k], w1 = lst[k + 32], w2 = lst[k + 64], w3 = lst[k + 96];
-      c += (probe(w0) + probe(w1)) + (probe(w2) + probe(w3));
-      if (sorted && __shfl_sync(LAGR_FULL_MASK, w3, 31) <= rx) {  // the round's last position
-        base = len_s;
-        break;
+    if (sorted) {
+      // four loads per lane in flight; the walk stops after the first 32-entry group whose last
+      // entry is at or below rx
+      for (; base + 128 <= len_s; base += 128) {
+        const int32_t k = base + lane;
+        const int32_t w0 = lst[k], w1 = lst[k + 32], w2 = lst[k + 64], w3 = lst[k + 96];
+        c += probe(w0);
+        if (__shfl_sync(LAGR_FULL_MASK, w0, 31) <= rx) { base = len_s; break; }
+        c += probe(w1);
+        if (__shfl_sync(LAGR_FULL_MASK, w1, 31) <= rx) { base = len_s; break; }
+        c += probe(w2);
+        if (__shfl_sync(LAGR_FULL_MASK, w2, 31) <= rx) { base = len_s; break; }
+        c += probe(w3);
+        if (__shfl_sync(LAGR_FULL_MASK, w3, 31) <= rx) { base = len_s; break; }
+      }
+    } else {
+      for (; base + 128 <= len_s; base += 128) {  // four loads per lane in flight
+        const int32_t k = base + lane;
+        const int32_t w0 = lst[k], w1 = lst[k + 32], w2 = lst[k + 64], w3 = lst[k + 96];
+        c += (probe(w0) + probe(w1)) + (probe(w2) + probe(w3));
       }
     }
     for (; base < len_s; base += 32) {

@@ -240,6 +240,23 @@ def test_pagerank_directed(L, dangling):
     pr_close(r.cpu().numpy(), ro)
 
 
+@pytest.mark.parametrize("directed,dangling", [(False, False), (True, True)])
+def test_pagerank_rmat16_and_er(L, directed, dangling):
+    # many warp items and heavy-row chunks per gather; twice on one graph (cached row plans), then
+    # a graph of short rows only
+    g = gen.rmat(16, 16, seed=61, directed=directed)
+    G = dev(L, g)
+    flags = L.LAGR_PR_DANGLING if dangling else 0
+    ro, ito, _ = oracle.pagerank(g, 0.85, 1e-7, 100, dangling)
+    for _ in range(2):
+        r, it = L.lagr_pagerank(G, 0.85, 1e-7, 100, flags=flags)
+        pr_close(r.cpu().numpy(), ro)
+        assert abs(it - ito) <= 2
+    ge = gen.erdos_renyi(40000, 6, seed=62)
+    r, _ = L.lagr_pagerank(dev(L, ge), 0.85, 1e-7, 100)
+    pr_close(r.cpu().numpy(), oracle.pagerank(ge, 0.85, 1e-7, 100)[0])
+
+
 def test_pagerank_fixed_iterations_and_heavy_rows(L):
     g = gen.concat([gen.star(9000), gen.rmat(12, 16, seed=3)])   # a row longer than the CTA threshold
     G = dev(L, g)
