@@ -172,9 +172,8 @@ def run_gpu(args):
             t = L.lagr_tc(G, L.LAGR_TC_AUTO)
         if marks is not None:
             marks[1].record(stream)
-        if only in ("all", "bfs"):
-            for i, s in enumerate(srcs):
-                L.lagr_bfs(G, s, 0, level=lvl_o[i], parent=par_o[i])
+        if only in ("all", "bfs"):  # the 16 traversals interleaved on the library's side streams
+            L.lagr_bfs_multi(G, srcs, 0, level=lvl_o, parent=par_o)
         if marks is not None:
             marks[2].record(stream)
         if only in ("all", "pr"):

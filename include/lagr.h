@@ -224,6 +224,23 @@ int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G, int3
              int32_t flags, void *stream, char *msg);
 
 /*
+ * Independent parents BFS from k sources (k <= LAGR_BFS_MULTI_MAX), each the
+ * traversal of lagr_bfs (Alg. 1 / 2, Sec. IV-A) with the same flags: row t of
+ * level / parent (device [k][n], row-major; either may be NULL) holds source
+ * src[t]'s result, depth (host [k] or NULL) its level count.  The traversals
+ * run interleaved on the library's side streams (they start after the work
+ * queued on `stream`, which waits for them before the call returns), so one
+ * host synchronisation per round serves all of them and their narrow levels
+ * run side by side.  Duplicate sources are allowed.  G's last_* statistics are
+ * those of src[k-1].  src: host [k].  Synchronises the stream.  Errors:
+ * NULL_POINTER, INVALID_VALUE (k, a source out of range, bad flags),
+ * OUT_OF_MEMORY, TIMEOUT, CUDA.
+ */
+#define LAGR_BFS_MULTI_MAX 64
+int lagr_bfs_multi(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G, const int32_t *src, int32_t k,
+                   int32_t flags, void *stream, char *msg);
+
+/*
  * lagr_bfs_noalloc: the parents BFS of lagr_bfs for callers that cannot allocate device memory
  * (the paper has no counterpart; it exists for users whose device memory is fixed up front by
  * another owner, or who must not enter the allocator while other work runs).  It takes the

@@ -9,7 +9,7 @@ raises when CUDA or the compiled library is unavailable.
 
 Entry points (same names as the C ABI): ``lagr_graph_new``, ``lagr_graph_free``,
 ``lagr_graph_check``, ``lagr_property_AT``, ``lagr_tc``, ``lagr_bfs``,
-``lagr_bfs_batch64``, ``lagr_pagerank``, ``lagr_pagerank_backward``,
+``lagr_bfs_multi``, ``lagr_bfs_batch64``, ``lagr_pagerank``, ``lagr_pagerank_backward``,
 ``lagr_batch_plan`` / ``lagr_batch_run`` / ``lagr_batch_free``, plus the
 ``PageRankFunction`` autograd wrapper.
 """
@@ -105,6 +105,7 @@ _SIGNATURES = {
     "lagr_property_row_degree": ([_G, _vp, _str], ctypes.c_int),
     "lagr_tc": ([ctypes.POINTER(ctypes.c_uint64), _G, _i32, _vp, _str], ctypes.c_int),
     "lagr_bfs": ([_vp, _vp, ctypes.POINTER(_i32), _G, _i32, _i32, _vp, _str], ctypes.c_int),
+    "lagr_bfs_multi": ([_vp, _vp, _vp, _G, _vp, _i32, _i32, _vp, _str], ctypes.c_int),
     "lagr_bfs_batch64": ([_vp, _G, ctypes.POINTER(_i32), _i32, _vp, _str], ctypes.c_int),
     "lagr_bfs_noalloc": ([_vp, _vp, ctypes.POINTER(_i32), _i32, _i64, _vp, _vp, _i32, _vp, _str], ctypes.c_int),
     "lagr_pagerank": ([_vp, ctypes.POINTER(_i32), _G, _f32, _f32, _i32, _vp, _i32, _vp, _str], ctypes.c_int),
@@ -266,6 +267,33 @@ def lagr_bfs(G: Graph, src: int, flags: int = 0, level=None, parent=None, want_l
                                  _stream(stream), msg)
     _check(rc, msg, "lagr_bfs")
     return level, parent, int(depth.value)
+
+
+LAGR_BFS_MULTI_MAX = 64
+
+
+def lagr_bfs_multi(G: Graph, srcs, flags: int = 0, level=None, parent=None, want_level: bool = True,
+                   want_parent: bool = True, stream=None):
+    """Independent parents BFS from each of `srcs` (at most 64), interleaved on side streams.
+    Returns (level [k, n], parent [k, n], depths); outputs may be passed in."""
+    torch = _torch()
+    srcs = [int(x) for x in srcs]
+    k = len(srcs)
+    if want_level and level is None:
+        level = torch.empty((k, G.n), dtype=torch.int32, device=G.rowptr.device)
+    if want_parent and parent is None:
+        parent = torch.empty((k, G.n), dtype=torch.int32, device=G.rowptr.device)
+    for t, name in ((level, "level"), (parent, "parent")):
+        _dev(t, torch.int32, name)
+        if t is not None and tuple(t.shape) != (k, G.n):
+            raise ValueError(f"{name} must have shape ({k}, {G.n})")
+    src = (ctypes.c_int32 * max(k, 1))(*srcs)
+    depth = (ctypes.c_int32 * max(k, 1))()
+    msg = _msg()
+    rc = load_library().lagr_bfs_multi(_ptr(level), _ptr(parent), depth, G.handle, src, k, flags,
+                                       _stream(stream), msg)
+    _check(rc, msg, "lagr_bfs_multi")
+    return level, parent, [int(depth[i]) for i in range(k)]
 
 
 LAGR_BFS_NOALLOC_MAX_N = 1 << 21

@@ -13,9 +13,14 @@
 // Narrow frontiers (the high-diameter regime of the paper's road graph) run many levels inside
 // one single-CTA launch with only __syncthreads between levels.  The push/pull choice is
 // Beamer's rule: pull when the frontier's edges exceed the unexplored edges / alpha, push again
-// when the frontier shrinks below n / beta.
+// when the frontier shrinks below n / beta.  The host takes that choice between phases from
+// counters the kernels store into mapped host memory; lagr_bfs_multi interleaves the phases of
+// several independent traversals on side streams.
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <utility>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -735,58 +740,64 @@ __global__ void bfs64_clear(const int32_t *__restrict__ flist, int32_t nf, unsig
 
 using namespace lagr;
 
-extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G, int32_t src, int32_t flags,
-                        void *stream, char *msg) {
-  LAGR_TRY(check_graph_arg(G, msg));
-  if (src < 0 || src >= G->n) {
-    set_msg(msg, "source %d out of range [0, %d)", src, G->n);
-    return LAGR_ERR_INVALID_VALUE;
-  }
-  if (flags & ~(LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY) ||
-      (flags & (LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY)) == (LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY)) {
-    set_msg(msg, "bad BFS flags 0x%x", flags);
-    return LAGR_ERR_INVALID_VALUE;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  Priv *P = nullptr;
-  LAGR_TRY(priv_get(G, s, msg, &P));
-  const bool push_only = flags & LAGR_BFS_PUSH_ONLY;
-  const bool pull_only = flags & LAGR_BFS_PULL_ONLY;
-  if (!push_only) LAGR_TRY(lagr_property_AT(G, s, msg));
-  const int32_t n = G->n;
-  const int64_t nwords = ((int64_t)n + 31) / 32;
-  Temp<uint32_t> visited(s), fbits(s), nbits(s);
-  Temp<int32_t> qa(s), qb(s), fdeg(s), offs(s);
-  Temp<int64_t> cnt(s);
-  LAGR_TRY(visited.alloc(nwords, msg, "visited bitmap"));
-  LAGR_TRY(fbits.alloc(nwords, msg, "frontier bitmap"));
-  LAGR_TRY(nbits.alloc(nwords, msg, "next frontier bitmap"));
-  LAGR_TRY(qa.alloc(n, msg, "frontier queue"));
-  LAGR_TRY(qb.alloc(n, msg, "frontier queue"));
-  LAGR_TRY(fdeg.alloc(n, msg, "frontier degrees"));
-  LAGR_TRY(offs.alloc((size_t)n + 1, msg, "frontier edge offsets"));
-  LAGR_TRY(cnt.alloc(B_NSLOT, msg, "BFS counters"));
-  bfs_init<<<grid_for(n, 256), 256, 0, s>>>(n, level, parent, visited.p, nwords);
-  bfs_seed<<<1, 1, 0, s>>>(G->rowptr, G->nnz, src, level, parent, visited.p, qa.p, cnt.p, P->hscal_dev);
-  LAGR_LAUNCH_CHECK();
+namespace lagr {
+namespace {
 
-  // pinned mirror of the counters: bfs_seed, bfs_push_small and bfs_advance store them there
-  const int64_t *h = P->hscal;
-  auto sync_counters = [&]() -> int {
-    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
-    return LAGR_OK;
-  };
-  // frontier representation: 0 = queue (push), 1 = bitmap fbits (pull)
-  int rep = 0;
+// One direction-optimising parents BFS (Alg. 1 / 2) as a host-side state machine on its own stream.
+// launch() takes the counters of the last phase from the mapped host mirror h (the phase's last
+// kernel stores them there), applies the direction rule and enqueues the next phase: several
+// narrow push levels in one CTA, one wide push level, or one pull level.  After the stream has been
+// synchronised, settle() does the phase's bookkeeping.  Several runs interleave their phases on
+// several streams, so one synchronisation serves them all (lagr_bfs_multi).
+struct BfsRun {
+  lagr_graph G = nullptr;
+  int32_t src = 0;
+  int32_t *level = nullptr, *parent = nullptr;
+  bool push_only = false, pull_only = false;
+  cudaStream_t s = nullptr;
+  int64_t *h = nullptr, *hd = nullptr;  // B_NSLOT counters: host view, device view
+  Temp<uint32_t> visited, fbits, nbits;
+  Temp<int32_t> qa, qb, fdeg, offs;
+  Temp<int64_t> cnt;
+  int rep = 0;  // frontier representation: 0 = queue (push), 1 = bitmap fbits (pull)
   int pushes = 0, pulls = 0;
   int32_t last_lev = 0;  // deepest level that discovered a vertex
-  LAGR_TRY(sync_counters());
   bool pull = false;     // direction of the previous level
   int64_t prev_nq = 0;   // frontier size before the last level
-  for (;;) {
+  bool done = false;
+  int phase = 0;         // what the last launch enqueued: 1 narrow push, 2 wide push, 3 pull
+  int32_t lev0 = 0;      // the level count before it
+
+  explicit BfsRun(cudaStream_t st)
+      : s(st), visited(st), fbits(st), nbits(st), qa(st), qb(st), fdeg(st), offs(st), cnt(st) {}
+
+  int start(char *msg) {
+    const int32_t n = G->n;
+    const int64_t nwords = ((int64_t)n + 31) / 32;
+    LAGR_TRY(visited.alloc(nwords, msg, "visited bitmap"));
+    LAGR_TRY(fbits.alloc(nwords, msg, "frontier bitmap"));
+    LAGR_TRY(nbits.alloc(nwords, msg, "next frontier bitmap"));
+    LAGR_TRY(qa.alloc(n, msg, "frontier queue"));
+    LAGR_TRY(qb.alloc(n, msg, "frontier queue"));
+    LAGR_TRY(fdeg.alloc(n, msg, "frontier degrees"));
+    LAGR_TRY(offs.alloc((size_t)n + 1, msg, "frontier edge offsets"));
+    LAGR_TRY(cnt.alloc(B_NSLOT, msg, "BFS counters"));
+    bfs_init<<<grid_for(n, 256), 256, 0, s>>>(n, level, parent, visited.p, nwords);
+    bfs_seed<<<1, 1, 0, s>>>(G->rowptr, G->nnz, src, level, parent, visited.p, qa.p, cnt.p, hd);
+    LAGR_LAUNCH_CHECK();
+    return LAGR_OK;
+  }
+
+  int launch(char *msg) {
+    const int32_t n = G->n;
+    const int64_t nwords = ((int64_t)n + 31) / 32;
     const int64_t nq = h[B_NQ], mf = h[B_MF], mu = h[B_MU];
     const int32_t lev = (int32_t)h[B_LEV];
-    if (nq == 0) break;
+    lev0 = lev;
+    if (nq == 0) {
+      done = true;
+      return LAGR_OK;
+    }
     if (lev + 1 > n) {
       set_msg(msg, "BFS exceeded n levels");
       return LAGR_ERR_TIMEOUT;
@@ -813,21 +824,10 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
         {
           KTimer kt(TK_BFS_SMALL, s);
           bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level, parent,
-                                                     cnt.p, n, push_only ? 0 : 1, P->hscal_dev);
+                                                     cnt.p, n, push_only ? 0 : 1, hd);
         }
         LAGR_LAUNCH_CHECK();
-        LAGR_TRY(sync_counters());
-        const int32_t done = (int32_t)h[B_LEV] - lev;
-        if (h[B_EXIT] == 4) {
-          set_msg(msg, "BFS exceeded n levels");
-          return LAGR_ERR_TIMEOUT;
-        }
-        if (done <= 0) {
-          set_msg(msg, "internal: narrow-frontier kernel made no progress");
-          return LAGR_ERR_TIMEOUT;
-        }
-        pushes += done;
-        last_lev = (h[B_NQ] > 0) ? (int32_t)h[B_LEV] : (int32_t)h[B_LEV] - 1;
+        phase = 1;
       } else {
         // wide push, balanced over the frontier's edges: degrees, their prefix, one CTA per
         // LB_CHUNK edges; the next frontier comes back as the bitmap nbits
@@ -841,17 +841,13 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
           bfs_push_lb<<<(unsigned)(nchunks > 0 ? nchunks : 1), 256, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, offs.p,
                                                                            visited.p, nbits.p, level, parent, cnt.p);
         }
-        bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0, P->hscal_dev);
+        bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0, hd);
         LAGR_LAUNCH_CHECK();
-        uint32_t *t = fbits.p;
-        fbits.p = nbits.p;
-        nbits.p = t;
+        std::swap(fbits.p, nbits.p);
         rep = 1;
-        LAGR_TRY(sync_counters());
-        pushes++;
-        if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
+        phase = 2;
       }
-      continue;
+      return LAGR_OK;
     }
     // pull level
     if (rep == 0) {  // queue -> bitmap
@@ -866,21 +862,209 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
                                                                           fbits.p, nbits.p, visited.p, level, parent,
                                                                           cnt.p);
     }
-    bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0, P->hscal_dev);
+    bfs_advance<<<1, 1, 0, s>>>(cnt.p, 0, hd);
     LAGR_LAUNCH_CHECK();
-    {
-      uint32_t *t = fbits.p;
-      fbits.p = nbits.p;
-      nbits.p = t;
-    }
-    LAGR_TRY(sync_counters());
-    pulls++;
-    if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
+    std::swap(fbits.p, nbits.p);
+    phase = 3;
+    return LAGR_OK;
   }
-  G->last_levels = last_lev + 1;
-  G->last_push_levels = pushes;
-  G->last_pull_levels = pulls;
-  if (depth) *depth = last_lev + 1;
+
+  int settle(char *msg) {
+    if (phase == 1) {
+      const int32_t levs = (int32_t)h[B_LEV] - lev0;
+      if (h[B_EXIT] == 4) {
+        set_msg(msg, "BFS exceeded n levels");
+        return LAGR_ERR_TIMEOUT;
+      }
+      if (levs <= 0) {
+        set_msg(msg, "internal: narrow-frontier kernel made no progress");
+        return LAGR_ERR_TIMEOUT;
+      }
+      pushes += levs;
+      last_lev = (h[B_NQ] > 0) ? (int32_t)h[B_LEV] : (int32_t)h[B_LEV] - 1;
+    } else {
+      if (phase == 2) pushes++;
+      else pulls++;
+      if (h[B_NQ] > 0) last_lev = (int32_t)h[B_LEV];
+    }
+    phase = 0;
+    return LAGR_OK;
+  }
+};
+
+int check_bfs_flags(int32_t flags, char *msg) {
+  if (flags & ~(LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY) ||
+      (flags & (LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY)) == (LAGR_BFS_PUSH_ONLY | LAGR_BFS_PULL_ONLY)) {
+    set_msg(msg, "bad BFS flags 0x%x", flags);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  return LAGR_OK;
+}
+
+// The library's side streams for interleaved runs (per device, created once, non-blocking)
+constexpr int BFS_STREAMS = 8;
+std::mutex g_bfs_stream_mu;
+cudaStream_t g_bfs_streams[64][BFS_STREAMS];
+
+int bfs_streams(cudaStream_t **out, char *msg) {
+  int d = 0;
+  LAGR_CUDA_TRY(cudaGetDevice(&d));
+  if (d < 0 || d >= 64) {
+    set_msg(msg, "device %d out of range", d);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  std::lock_guard<std::mutex> lk(g_bfs_stream_mu);
+  for (int i = 0; i < BFS_STREAMS; i++)
+    if (!g_bfs_streams[d][i]) LAGR_CUDA_TRY(cudaStreamCreateWithFlags(&g_bfs_streams[d][i], cudaStreamNonBlocking));
+  *out = g_bfs_streams[d];
+  return LAGR_OK;
+}
+
+// the mapped host mirrors of k runs: B_NSLOT counters each, LAGR_NHOST / B_NSLOT runs per block
+struct Mirrors {
+  std::vector<HostBlock> blocks;
+  ~Mirrors() {
+    for (const HostBlock &b : blocks) host_block_put(b);
+  }
+  int get(int k, char *msg) {
+    constexpr int per = LAGR_NHOST / B_NSLOT;
+    for (int i = 0; i < (k + per - 1) / per; i++) {
+      HostBlock b;
+      if (!host_block_get(&b)) {
+        set_msg(msg, "out of pinned host memory");
+        return LAGR_ERR_OUT_OF_MEMORY;
+      }
+      blocks.push_back(b);
+    }
+    return LAGR_OK;
+  }
+  int64_t *host(int t) const { return blocks[t / (LAGR_NHOST / B_NSLOT)].h + (t % (LAGR_NHOST / B_NSLOT)) * B_NSLOT; }
+  int64_t *dev(int t) const { return blocks[t / (LAGR_NHOST / B_NSLOT)].d + (t % (LAGR_NHOST / B_NSLOT)) * B_NSLOT; }
+};
+
+}  // namespace
+}  // namespace lagr
+
+extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G, int32_t src, int32_t flags,
+                        void *stream, char *msg) {
+  LAGR_TRY(check_graph_arg(G, msg));
+  if (src < 0 || src >= G->n) {
+    set_msg(msg, "source %d out of range [0, %d)", src, G->n);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  LAGR_TRY(check_bfs_flags(flags, msg));
+  cudaStream_t s = (cudaStream_t)stream;
+  Priv *P = nullptr;
+  LAGR_TRY(priv_get(G, s, msg, &P));
+  if (!(flags & LAGR_BFS_PUSH_ONLY)) LAGR_TRY(lagr_property_AT(G, s, msg));
+  Mirrors mir;
+  LAGR_TRY(mir.get(1, msg));
+  BfsRun r(s);
+  r.G = G;
+  r.src = src;
+  r.level = level;
+  r.parent = parent;
+  r.push_only = flags & LAGR_BFS_PUSH_ONLY;
+  r.pull_only = flags & LAGR_BFS_PULL_ONLY;
+  r.h = mir.host(0);
+  r.hd = mir.dev(0);
+  LAGR_TRY(r.start(msg));
+  for (;;) {
+    LAGR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (r.phase) LAGR_TRY(r.settle(msg));
+    LAGR_TRY(r.launch(msg));
+    if (r.done) break;
+  }
+  G->last_levels = r.last_lev + 1;
+  G->last_push_levels = r.pushes;
+  G->last_pull_levels = r.pulls;
+  if (depth) *depth = r.last_lev + 1;
+  clear_msg(msg);
+  return LAGR_OK;
+}
+
+extern "C" int lagr_bfs_multi(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G, const int32_t *src,
+                              int32_t k, int32_t flags, void *stream, char *msg) {
+  LAGR_TRY(check_graph_arg(G, msg));
+  if (!src) {
+    set_msg(msg, "src is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  if (k < 1 || k > LAGR_BFS_MULTI_MAX) {
+    set_msg(msg, "k must be in [1, %d], got %d", LAGR_BFS_MULTI_MAX, k);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  for (int i = 0; i < k; i++)
+    if (src[i] < 0 || src[i] >= G->n) {
+      set_msg(msg, "source %d (index %d) out of range", src[i], i);
+      return LAGR_ERR_INVALID_VALUE;
+    }
+  LAGR_TRY(check_bfs_flags(flags, msg));
+  cudaStream_t s = (cudaStream_t)stream;
+  Priv *P = nullptr;
+  LAGR_TRY(priv_get(G, s, msg, &P));
+  if (!(flags & LAGR_BFS_PUSH_ONLY)) LAGR_TRY(lagr_property_AT(G, s, msg));
+  cudaStream_t *side = nullptr;
+  LAGR_TRY(bfs_streams(&side, msg));
+  const int ns = k < BFS_STREAMS ? k : BFS_STREAMS;
+  Mirrors mir;
+  LAGR_TRY(mir.get(k, msg));
+  // the side streams start after the work queued on the caller's stream, which waits for them at
+  // the end.  On an error return the join first waits for the side streams, so that no kernel
+  // still writes a host mirror when the mirrors go back to the pool.
+  cudaEvent_t ev[BFS_STREAMS + 1] = {};
+  for (int i = 0; i <= ns; i++) LAGR_CUDA_TRY(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+  struct Join {
+    cudaEvent_t *ev;
+    cudaStream_t s, *side;
+    int ns;
+    ~Join() {
+      for (int i = 0; i < ns; i++) {
+        cudaStreamSynchronize(side[i]);
+        cudaEventRecord(ev[i + 1], side[i]);
+        cudaStreamWaitEvent(s, ev[i + 1], 0);
+      }
+      for (int i = 0; i <= ns; i++) cudaEventDestroy(ev[i]);
+    }
+  };
+  LAGR_CUDA_TRY(cudaEventRecord(ev[0], s));
+  for (int i = 0; i < ns; i++) LAGR_CUDA_TRY(cudaStreamWaitEvent(side[i], ev[0], 0));
+  const int64_t n = G->n;
+  std::vector<std::unique_ptr<BfsRun>> runs;
+  {
+    Join join{ev, s, side, ns};
+    for (int t = 0; t < k; t++) {
+      runs.emplace_back(new BfsRun(side[t % ns]));
+      BfsRun &r = *runs.back();
+      r.G = G;
+      r.src = src[t];
+      r.level = level ? level + (int64_t)t * n : nullptr;
+      r.parent = parent ? parent + (int64_t)t * n : nullptr;
+      r.push_only = flags & LAGR_BFS_PUSH_ONLY;
+      r.pull_only = flags & LAGR_BFS_PULL_ONLY;
+      r.h = mir.host(t);
+      r.hd = mir.dev(t);
+      LAGR_TRY(r.start(msg));
+    }
+    for (;;) {
+      for (int i = 0; i < ns; i++) LAGR_CUDA_TRY(cudaStreamSynchronize(side[i]));
+      bool active = false;
+      for (auto &rp : runs) {
+        if (rp->done) continue;
+        if (rp->phase) LAGR_TRY(rp->settle(msg));
+        LAGR_TRY(rp->launch(msg));
+        active = active || !rp->done;
+      }
+      if (!active) break;
+    }
+    for (int t = 0; t < k; t++)
+      if (depth) depth[t] = runs[t]->last_lev + 1;
+    const BfsRun &last = *runs.back();
+    G->last_levels = last.last_lev + 1;
+    G->last_push_levels = last.pushes;
+    G->last_pull_levels = last.pulls;
+    runs.clear();  // the work space is freed on the side streams before the join
+  }
   clear_msg(msg);
   return LAGR_OK;
 }

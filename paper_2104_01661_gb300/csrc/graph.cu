@@ -94,13 +94,10 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
 // Pinned host mirrors of the device scalars (LAGR_NHOST int64 each, with their device-mapped
 // addresses), recycled between graphs and calls: allocating and freeing pinned memory per graph
 // costs a device-wide synchronisation in the free.
-struct HostBlock {
-  int64_t *h, *d;
-};
 static std::mutex g_host_mu;
 static std::vector<HostBlock> g_host_free;
 
-static bool host_block_get(HostBlock *b) {
+bool host_block_get(HostBlock *b) {
   {
     std::lock_guard<std::mutex> lk(g_host_mu);
     if (!g_host_free.empty()) {
@@ -124,7 +121,7 @@ static bool host_block_get(HostBlock *b) {
   return true;
 }
 
-static void host_block_put(HostBlock b) {
+void host_block_put(HostBlock b) {
   std::lock_guard<std::mutex> lk(g_host_mu);
   g_host_free.push_back(b);
 }

@@ -149,6 +149,13 @@ int priv_get(lagr_graph G, cudaStream_t s, char *msg, Priv **out);
 // contiguous bytes (a multiple of 4, at most LAGR_NHOST * 8); fetch_i32s gathers `count` (<= 8)
 // scalars from separate addresses.
 int fetch_to_host(void *dst, const void *dsrc, size_t bytes, cudaStream_t s, char *msg);
+// the recycled pinned, device-mapped blocks behind them (LAGR_NHOST int64 each: h for the host,
+// d for kernels); get returns false when pinned memory runs out
+struct HostBlock {
+  int64_t *h, *d;
+};
+bool host_block_get(HostBlock *b);
+void host_block_put(HostBlock b);
 int fetch_i32s(int32_t *dst, const int32_t *const *srcs, int count, cudaStream_t s, char *msg);
 
 // build (once; no-op when pl->nblk >= 0) the row plan of a CSR.  Synchronises the stream.

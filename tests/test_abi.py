@@ -98,6 +98,13 @@ def test_entry_point_validation(lib):
     assert lib.lagr_bfs(None, None, None, G, -1, 0, None, msg) == L.LAGR_ERR_INVALID_VALUE
     assert lib.lagr_bfs(None, None, None, G, 0, 3, None, msg) == L.LAGR_ERR_INVALID_VALUE
     src = (ctypes.c_int32 * 2)(0, 1)
+    assert lib.lagr_bfs_multi(None, None, None, G, None, 2, 0, None, msg) == L.LAGR_ERR_NULL_POINTER
+    assert lib.lagr_bfs_multi(None, None, None, G, src, 0, 0, None, msg) == L.LAGR_ERR_INVALID_VALUE
+    assert lib.lagr_bfs_multi(None, None, None, G, src, 65, 0, None, msg) == L.LAGR_ERR_INVALID_VALUE
+    assert lib.lagr_bfs_multi(None, None, None, G, src, 2, 3, None, msg) == L.LAGR_ERR_INVALID_VALUE
+    assert lib.lagr_bfs_multi(None, None, None, G, (ctypes.c_int32 * 2)(0, 4), 2, 0, None, msg) == \
+        L.LAGR_ERR_INVALID_VALUE
+    assert b"out of range" in msg.value
     assert lib.lagr_bfs_batch64(FAKE, G, src, 0, None, msg) == L.LAGR_ERR_INVALID_VALUE
     assert lib.lagr_bfs_batch64(FAKE, G, src, 65, None, msg) == L.LAGR_ERR_INVALID_VALUE
     assert lib.lagr_bfs_batch64(FAKE, D, src, 2, None, msg) == L.LAGR_ERR_INVALID_GRAPH

@@ -188,6 +188,50 @@ def test_bfs_erdos_renyi_pull_heavy(L):
     assert G.struct.last_pull_levels >= 1
 
 
+@pytest.mark.parametrize("flags", [0, 1, 2])
+def test_bfs_multi_matches_single(L, rmat12, flags):
+    # independent traversals interleaved on side streams: duplicates, an isolated source, more
+    # sources than side streams
+    G = dev(L, rmat12)
+    iso = int(np.nonzero(rmat12.degree() == 0)[0][0]) if (rmat12.degree() == 0).any() else 0
+    srcs = [int(x) for x in gen.sources(rmat12, 17, seed=31)] + [iso, 5, 5]
+    lv, par, depths = L.lagr_bfs_multi(G, srcs, flags)
+    lv, par = lv.cpu().numpy(), par.cpu().numpy()
+    for t, s in enumerate(srcs):
+        olevel, _, odepth = oracle.bfs(rmat12, s)
+        assert np.array_equal(lv[t], olevel), t
+        assert depths[t] == odepth
+        check_parents(rmat12, lv[t], par[t], s)
+
+
+def test_bfs_multi_directed_and_limits(L):
+    import torch
+    g = gen.rmat(13, 8, seed=11, directed=True)
+    G = dev(L, g)
+    srcs = [int(x) for x in gen.sources(g, 3, seed=4)]
+    lv, par, depths = L.lagr_bfs_multi(G, srcs)
+    for t, s in enumerate(srcs):
+        olevel, _, odepth = oracle.bfs(g, s)
+        assert np.array_equal(lv[t].cpu().numpy(), olevel) and depths[t] == odepth
+        check_parents(g, lv[t].cpu().numpy(), par[t].cpu().numpy(), s)
+    ge = gen.erdos_renyi(5000, 6, seed=9)
+    Ge = dev(L, ge)
+    srcs = list(range(0, 5000, 79))[:64]  # the maximum k
+    lv, par, _ = L.lagr_bfs_multi(Ge, srcs, want_parent=False)
+    assert par is None and lv.shape == (64, 5000)
+    for t in (0, 31, 63):
+        assert np.array_equal(lv[t].cpu().numpy(), oracle.bfs(ge, srcs[t])[0])
+    _, par1, d1 = L.lagr_bfs_multi(Ge, [17], want_level=False)
+    check_parents(ge, oracle.bfs(ge, 17)[0], par1[0].cpu().numpy(), 17)
+    assert d1[0] == oracle.bfs(ge, 17)[2]
+    # the caller's stream: the results are there once the call returns on a side stream of torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        lv2, _, _ = L.lagr_bfs_multi(Ge, [3, 4], stream=s)
+    s.synchronize()
+    assert np.array_equal(lv2[1].cpu().numpy(), oracle.bfs(ge, 4)[0])
+
+
 def test_bfs_outputs_optional(L, rmat12):
     G = dev(L, rmat12)
     lvl, par, depth = L.lagr_bfs(G, 0, want_parent=False)
