@@ -322,10 +322,34 @@ __device__ __forceinline__ int32_t shfl_cmpx(int32_t x, int j, bool desc, int la
   return (((lane & j) == 0) == desc) ? max(x, y) : min(x, y);
 }
 
-// Bitonic sort of one row of at most P entries by one warp, entirely in registers: element i sits in
-// lane i % 32, register i / 32.  A stage of partner distance j >= 32 pairs registers of the same lane;
-// below 32 it pairs lanes (shuffles).  The direction of every pair is fixed by the unrolled loops
-// except in the stages with merge size k <= 16.
+// one stage of partner distance 32 * JR between the registers of one lane (element i = lane + 32 r
+// sits in register r): in a descending segment (bit k of i clear) the lower index keeps the larger
+template <int R, int JR>
+__device__ __forceinline__ void cx_regs(int32_t (&v)[R], int k) {
+#pragma unroll
+  for (int r = 0; r < R; r++)
+    if ((r & JR) == 0) {
+      const bool desc = ((32 * r) & k) == 0;
+      const int32_t a = v[r], b = v[r | JR];
+      v[r] = desc ? max(a, b) : min(a, b);
+      v[r | JR] = desc ? min(a, b) : max(a, b);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void cx_regs_any(int32_t (&v)[R], int jr, int k) {
+  if constexpr (R >= 2) if (jr == 1) return cx_regs<R, 1>(v, k);
+  if constexpr (R >= 4) if (jr == 2) return cx_regs<R, 2>(v, k);
+  if constexpr (R >= 8) if (jr == 4) return cx_regs<R, 4>(v, k);
+  if constexpr (R >= 16) if (jr == 8) return cx_regs<R, 8>(v, k);
+  if constexpr (R >= 32) if (jr == 16) return cx_regs<R, 16>(v, k);
+}
+
+// Bitonic sort of one row of at most P entries by one warp, in registers: element i sits in lane
+// i % 32, register i / 32.  A stage of partner distance j >= 32 pairs registers of one lane, below
+// 32 it pairs lanes (shuffles).  The stages run as loops over one unrolled copy of each kind of
+// stage, which keeps the code small (a fully unrolled network of 1024 entries alone is thousands
+// of instructions, more than the instruction caches hold for all the warps of an SM).
 template <int P>
 __device__ __forceinline__ void warp_sort_desc(int32_t *__restrict__ row, int32_t d, int lane) {
   constexpr int R = P / 32;
@@ -335,24 +359,14 @@ __device__ __forceinline__ void warp_sort_desc(int32_t *__restrict__ row, int32_
     const int32_t i = lane + 32 * r;
     v[r] = i < d ? row[i] : INT32_MIN;
   }
-#pragma unroll
+#pragma unroll 1
   for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll 1
+    for (int j = k >> 1; j >= 32; j >>= 1) cx_regs_any<R>(v, j >> 5, k);
+#pragma unroll 1
+    for (int j = min(k >> 1, 16); j > 0; j >>= 1) {
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-        const int jr = j >> 5;
-#pragma unroll
-        for (int r = 0; r < R; r++)
-          if ((r & jr) == 0) {
-            const bool desc = ((32 * r) & k) == 0;
-            const int32_t a = v[r], b = v[r | jr];
-            v[r] = desc ? max(a, b) : min(a, b);
-            v[r | jr] = desc ? min(a, b) : max(a, b);
-          }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; r++) v[r] = shfl_cmpx(v[r], j, ((lane + 32 * r) & k) == 0, lane);
-      }
+      for (int r = 0; r < R; r++) v[r] = shfl_cmpx(v[r], j, ((lane + 32 * r) & k) == 0, lane);
     }
   }
 #pragma unroll
