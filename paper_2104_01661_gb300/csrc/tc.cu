@@ -287,8 +287,9 @@ constexpr int TC_SORT_WARP = 1024;
 constexpr int TC_SORT_MAX = 16384;
 constexpr int TCS_WARPS = 4;  // warps per CTA of the warp sorter
 
-__global__ void tc_sort_collect(const int32_t *__restrict__ dplus, int32_t n, int32_t *__restrict__ listw,
-                                int32_t *__restrict__ listc, int64_t *__restrict__ dscal) {
+// the rows to sort, as (first entry, length) pairs: 32..TC_SORT_WARP entries to listw, longer to listc
+__global__ void tc_sort_collect(const int32_t *__restrict__ ustart, const int32_t *__restrict__ dplus, int32_t n,
+                                int2 *__restrict__ listw, int2 *__restrict__ listc, int64_t *__restrict__ dscal) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -302,8 +303,8 @@ __global__ void tc_sort_collect(const int32_t *__restrict__ dplus, int32_t n, in
     if (lane == 0 && bc) pc = atomicAdd((unsigned long long *)&dscal[SL_NSC], (unsigned long long)__popc(bc));
     pw = __shfl_sync(LAGR_FULL_MASK, pw, 0);
     pc = __shfl_sync(LAGR_FULL_MASK, pc, 0);
-    if (w) listw[pw + __popc(bw & lt)] = (int32_t)v;
-    if (c) listc[pc + __popc(bc & lt)] = (int32_t)v;
+    if (w) listw[pw + __popc(bw & lt)] = make_int2(ustart[v], d);
+    if (c) listc[pc + __popc(bc & lt)] = make_int2(ustart[v], d);
   }
 }
 
@@ -376,39 +377,41 @@ __device__ __forceinline__ void warp_sort_desc(int32_t *__restrict__ row, int32_
   }
 }
 
-// the rows of TC_SORT_MIN <= d+ <= TC_SORT_WARP: one warp each, in registers
+// the rows of TC_SORT_MIN <= d+ <= TC_SORT_WARP: one warp each, in registers; a warp takes every
+// nw-th row and loads the next row's pair while it sorts the current one
 __global__ void __launch_bounds__(TCS_WARPS * 32)
-    tc_sort_rows_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus,
-                      const int32_t *__restrict__ list, const int64_t *__restrict__ dscal,
+    tc_sort_rows_warp(const int2 *__restrict__ list, const int64_t *__restrict__ dscal,
                       int32_t *__restrict__ u_colidx) {
   const int lane = threadIdx.x & 31;
   const int64_t nl = dscal[SL_NSW];
   const int64_t nw = (int64_t)gridDim.x * TCS_WARPS;
-  for (int64_t it = (int64_t)blockIdx.x * TCS_WARPS + (threadIdx.x >> 5); it < nl; it += nw) {
-    const int32_t v = list[it];
-    const int32_t d = dplus[v];
-    int32_t *row = u_colidx + rowptr[v];
+  int64_t it = (int64_t)blockIdx.x * TCS_WARPS + (threadIdx.x >> 5);
+  int2 cur = it < nl ? list[it] : make_int2(0, 0);
+  for (; it < nl; it += nw) {
+    const int2 nxt = it + nw < nl ? list[it + nw] : make_int2(0, 0);
+    int32_t *row = u_colidx + cur.x;
+    const int32_t d = cur.y;
     if (d <= 32) warp_sort_desc<32>(row, d, lane);
     else if (d <= 64) warp_sort_desc<64>(row, d, lane);
     else if (d <= 128) warp_sort_desc<128>(row, d, lane);
     else if (d <= 256) warp_sort_desc<256>(row, d, lane);
     else if (d <= 512) warp_sort_desc<512>(row, d, lane);
     else warp_sort_desc<TC_SORT_WARP>(row, d, lane);
+    cur = nxt;
   }
 }
 
 // the rows of TC_SORT_WARP < d+ <= TC_SORT_MAX: one CTA each (dynamic shared memory TC_SORT_MAX ints)
 constexpr int TCS_CTA_THREADS = 1024;
 __global__ void __launch_bounds__(TCS_CTA_THREADS)
-    tc_sort_rows_cta(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus,
-                     const int32_t *__restrict__ list, const int64_t *__restrict__ dscal,
+    tc_sort_rows_cta(const int2 *__restrict__ list, const int64_t *__restrict__ dscal,
                      int32_t *__restrict__ u_colidx) {
   extern __shared__ int32_t sbig[];
   const int64_t nl = dscal[SL_NSC];
   for (int64_t it = blockIdx.x; it < nl; it += gridDim.x) {
-    const int32_t v = list[it];
-    const int32_t d = dplus[v];
-    int32_t *row = u_colidx + rowptr[v];
+    const int2 item = list[it];
+    const int32_t d = item.y;
+    int32_t *row = u_colidx + item.x;
     int32_t P = TC_SORT_WARP * 2;
     while (P < d) P <<= 1;
     for (int32_t i = threadIdx.x; i < P; i += blockDim.x) sbig[i] = i < d ? row[i] : INT32_MIN;
@@ -809,12 +812,20 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
     if (rp.nheavy > 0)
       tc_orient_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, G->u_dplus, G->u_colidx, rp.heavy,
                                               rp.nheavy);
-    {  // the rows to sort are listed in the rank-sort buffers (free again once the ranks are made)
-      int32_t *lw = P->tc_sortbuf, *lc = P->tc_sortbuf + n;
-      tc_sort_collect<<<grid_for(n, 256), 256, 0, s>>>(G->u_dplus, n, lw, lc, P->dscal);
-      tc_sort_rows_warp<<<152 * 8, TCS_WARPS * 32, 0, s>>>(G->rowptr, G->u_dplus, lw, P->dscal, G->u_colidx);
-      tc_sort_rows_cta<<<152, TCS_CTA_THREADS, TC_SORT_MAX * sizeof(int32_t), s>>>(G->rowptr, G->u_dplus, lc,
-                                                                                    P->dscal, G->u_colidx);
+    {  // the rows to sort are listed in the rank-sort buffers (4n ints, free again once the ranks
+       // are made): n pairs for the warp sorter, then n for the CTA sorter
+      int2 *lw = reinterpret_cast<int2 *>(P->tc_sortbuf), *lc = lw + n;
+      tc_sort_collect<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, lw, lc, P->dscal);
+      static int sort_ctas = 0;  // one wave of the warp sorter: every warp resident at once
+      if (sort_ctas == 0) {
+        int per_sm = 0, dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_sort_rows_warp, TCS_WARPS * 32, 0);
+        sort_ctas = (per_sm > 0 && nsm > 0) ? per_sm * nsm : 152 * 4;
+      }
+      tc_sort_rows_warp<<<sort_ctas, TCS_WARPS * 32, 0, s>>>(lw, P->dscal, G->u_colidx);
+      tc_sort_rows_cta<<<152, TCS_CTA_THREADS, TC_SORT_MAX * sizeof(int32_t), s>>>(lc, P->dscal, G->u_colidx);
     }
     tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, P->tc_listw, P->tc_listwh,
                                                  P->tc_capwh, P->tc_listc, P->tc_capc, P->dscal, prm.wmax,
