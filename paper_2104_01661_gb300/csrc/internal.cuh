@@ -137,6 +137,7 @@ enum ScalarSlot {
   SC_COUNT9 = 10,
   SC_COUNT10 = 11,
   SC_COUNT11 = 12,
+  SC_COUNT12 = 13,
   LAGR_NSCAL = 16,
   LAGR_NHOST = 64  // int64 slots of the pinned host mirror (also stages up to 64 int32 sources)
 };

@@ -53,8 +53,9 @@ constexpr int SL_QC = SC_COUNT6;
 constexpr int SL_TOTAL = SC_COUNT7;
 constexpr int SL_QWL = SC_COUNT8;  // queue cursor of the whole-anchor warp items
 constexpr int SL_NWF = SC_COUNT9;  // heavier warp anchors (one item each), stored from the front of listw
-constexpr int SL_NSW = SC_COUNT10;  // U rows listed for the warp sorter
+constexpr int SL_NSW = SC_COUNT10;  // U rows listed for the warp sorter, up to TC_SORT_SMALL entries
 constexpr int SL_NSC = SC_COUNT11;  // U rows listed for the CTA sorter
+constexpr int SL_NSM = SC_COUNT12;  // U rows listed for the warp sorter, longer than TC_SORT_SMALL
 
 __device__ __forceinline__ uint32_t hslot(int32_t w, int logT) {
   return ((uint32_t)w * 0x9E3779B1u) >> (32 - logT);
@@ -283,27 +284,36 @@ __global__ void tc_orient_heavy(const int32_t *__restrict__ rowptr, const int32_
 // shared memory above); shorter rows are probed entry by entry anyway, and longer rows keep their
 // order and are walked to the end.  The rows to sort are listed first.
 constexpr int TC_SORT_MIN = 32;
+constexpr int TC_SORT_SMALL = 256;  // rows up to this long are sorted by the low-register warp sorter
 constexpr int TC_SORT_WARP = 1024;
 constexpr int TC_SORT_MAX = 16384;
 constexpr int TCS_WARPS = 4;  // warps per CTA of the warp sorter
 
-// the rows to sort, as (first entry, length) pairs: 32..TC_SORT_WARP entries to listw, longer to listc
+// the rows to sort, as (first entry, length) pairs: TC_SORT_MIN..TC_SORT_SMALL entries to lists
+// from the front, TC_SORT_SMALL..TC_SORT_WARP to listm from its end backwards, longer to listc
+// from the front (listm and listc share n slots: a vertex is in at most one list)
 __global__ void tc_sort_collect(const int32_t *__restrict__ ustart, const int32_t *__restrict__ dplus, int32_t n,
-                                int2 *__restrict__ listw, int2 *__restrict__ listc, int64_t *__restrict__ dscal) {
+                                int2 *__restrict__ lists, int2 *__restrict__ listc, int2 *__restrict__ listm_end,
+                                int64_t *__restrict__ dscal) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t v = base + lane;
     const int32_t d = v < n ? dplus[v] : 0;
-    const bool w = d >= TC_SORT_MIN && d <= TC_SORT_WARP, c = d > TC_SORT_WARP && d <= TC_SORT_MAX;
-    const unsigned bw = __ballot_sync(LAGR_FULL_MASK, w), bc = __ballot_sync(LAGR_FULL_MASK, c);
-    unsigned long long pw = 0, pc = 0;
+    const bool w = d >= TC_SORT_MIN && d <= TC_SORT_SMALL, m = d > TC_SORT_SMALL && d <= TC_SORT_WARP,
+               c = d > TC_SORT_WARP && d <= TC_SORT_MAX;
+    const unsigned bw = __ballot_sync(LAGR_FULL_MASK, w), bm = __ballot_sync(LAGR_FULL_MASK, m),
+                   bc = __ballot_sync(LAGR_FULL_MASK, c);
+    unsigned long long pw = 0, pm = 0, pc = 0;
     if (lane == 0 && bw) pw = atomicAdd((unsigned long long *)&dscal[SL_NSW], (unsigned long long)__popc(bw));
+    if (lane == 0 && bm) pm = atomicAdd((unsigned long long *)&dscal[SL_NSM], (unsigned long long)__popc(bm));
     if (lane == 0 && bc) pc = atomicAdd((unsigned long long *)&dscal[SL_NSC], (unsigned long long)__popc(bc));
     pw = __shfl_sync(LAGR_FULL_MASK, pw, 0);
+    pm = __shfl_sync(LAGR_FULL_MASK, pm, 0);
     pc = __shfl_sync(LAGR_FULL_MASK, pc, 0);
-    if (w) listw[pw + __popc(bw & lt)] = make_int2(ustart[v], d);
+    if (w) lists[pw + __popc(bw & lt)] = make_int2(ustart[v], d);
+    if (m) *(listm_end - 1 - (int64_t)(pm + __popc(bm & lt))) = make_int2(ustart[v], d);
     if (c) listc[pc + __popc(bc & lt)] = make_int2(ustart[v], d);
   }
 }
@@ -377,28 +387,46 @@ __device__ __forceinline__ void warp_sort_desc(int32_t *__restrict__ row, int32_
   }
 }
 
-// the rows of TC_SORT_MIN <= d+ <= TC_SORT_WARP: one warp each, in registers; a warp takes every
-// nw-th row and loads the next row's pair while it sorts the current one
+// The listed rows of up to PMAX entries: one warp each, in registers; a warp takes every nw-th row
+// and loads the next row's pair while it sorts the current one.  Two instances: PMAX =
+// TC_SORT_SMALL for most rows (few registers, so many warps per SM hide the shuffle latencies),
+// PMAX = TC_SORT_WARP for the longer ones (list read backwards from its end when `back`).
+template <int PMAX>
 __global__ void __launch_bounds__(TCS_WARPS * 32)
-    tc_sort_rows_warp(const int2 *__restrict__ list, const int64_t *__restrict__ dscal,
+    tc_sort_rows_warp(const int2 *__restrict__ list, int back, const int64_t *__restrict__ dscal, int slot,
                       int32_t *__restrict__ u_colidx) {
   const int lane = threadIdx.x & 31;
-  const int64_t nl = dscal[SL_NSW];
+  const int64_t nl = dscal[slot];
   const int64_t nw = (int64_t)gridDim.x * TCS_WARPS;
+  auto at = [&](int64_t i) { return back ? list[-1 - i] : list[i]; };
   int64_t it = (int64_t)blockIdx.x * TCS_WARPS + (threadIdx.x >> 5);
-  int2 cur = it < nl ? list[it] : make_int2(0, 0);
+  int2 cur = it < nl ? at(it) : make_int2(0, 0);
   for (; it < nl; it += nw) {
-    const int2 nxt = it + nw < nl ? list[it + nw] : make_int2(0, 0);
+    const int2 nxt = it + nw < nl ? at(it + nw) : make_int2(0, 0);
     int32_t *row = u_colidx + cur.x;
     const int32_t d = cur.y;
     if (d <= 32) warp_sort_desc<32>(row, d, lane);
     else if (d <= 64) warp_sort_desc<64>(row, d, lane);
-    else if (d <= 128) warp_sort_desc<128>(row, d, lane);
-    else if (d <= 256) warp_sort_desc<256>(row, d, lane);
-    else if (d <= 512) warp_sort_desc<512>(row, d, lane);
-    else warp_sort_desc<TC_SORT_WARP>(row, d, lane);
+    else if (PMAX <= 128 || d <= 128) warp_sort_desc<(PMAX < 128 ? PMAX : 128)>(row, d, lane);
+    else if (PMAX <= 256 || d <= 256) warp_sort_desc<(PMAX < 256 ? PMAX : 256)>(row, d, lane);
+    else if (PMAX <= 512 || d <= 512) warp_sort_desc<(PMAX < 512 ? PMAX : 512)>(row, d, lane);
+    else warp_sort_desc<PMAX>(row, d, lane);
     cur = nxt;
   }
+}
+
+// one wave of a warp sorter instance: every warp resident at once
+template <int PMAX>
+int sort_wave_ctas() {
+  static int ctas = 0;
+  if (ctas == 0) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_sort_rows_warp<PMAX>, TCS_WARPS * 32, 0);
+    ctas = (per_sm > 0 && nsm > 0) ? per_sm * nsm : 152 * 4;
+  }
+  return ctas;
 }
 
 // the rows of TC_SORT_WARP < d+ <= TC_SORT_MAX: one CTA each (dynamic shared memory TC_SORT_MAX ints)
@@ -813,18 +841,13 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
       tc_orient_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, G->u_dplus, G->u_colidx, rp.heavy,
                                               rp.nheavy);
     {  // the rows to sort are listed in the rank-sort buffers (4n ints, free again once the ranks
-       // are made): n pairs for the warp sorter, then n for the CTA sorter
-      int2 *lw = reinterpret_cast<int2 *>(P->tc_sortbuf), *lc = lw + n;
-      tc_sort_collect<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, lw, lc, P->dscal);
-      static int sort_ctas = 0;  // one wave of the warp sorter: every warp resident at once
-      if (sort_ctas == 0) {
-        int per_sm = 0, dev = 0, nsm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_sort_rows_warp, TCS_WARPS * 32, 0);
-        sort_ctas = (per_sm > 0 && nsm > 0) ? per_sm * nsm : 152 * 4;
-      }
-      tc_sort_rows_warp<<<sort_ctas, TCS_WARPS * 32, 0, s>>>(lw, P->dscal, G->u_colidx);
+       // are made): n pairs for the short rows, then n shared by the CTA rows and the long ones
+      int2 *lw = reinterpret_cast<int2 *>(P->tc_sortbuf), *lc = lw + n, *lm_end = lw + 2 * (int64_t)n;
+      tc_sort_collect<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, lw, lc, lm_end, P->dscal);
+      tc_sort_rows_warp<TC_SORT_SMALL><<<sort_wave_ctas<TC_SORT_SMALL>(), TCS_WARPS * 32, 0, s>>>(
+          lw, 0, P->dscal, SL_NSW, G->u_colidx);
+      tc_sort_rows_warp<TC_SORT_WARP><<<sort_wave_ctas<TC_SORT_WARP>(), TCS_WARPS * 32, 0, s>>>(
+          lm_end, 1, P->dscal, SL_NSM, G->u_colidx);
       tc_sort_rows_cta<<<152, TCS_CTA_THREADS, TC_SORT_MAX * sizeof(int32_t), s>>>(lc, P->dscal, G->u_colidx);
     }
     tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, P->tc_listw, P->tc_listwh,
