@@ -52,9 +52,14 @@ def peaks():
 # ---------------------------------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling of the SM clock and the throttle reasons (every 50 ms).  Started before
+    the warm-up so that it is running when the timed steps begin; summary() keeps the samples whose
+    timestamps fall in the timed window (or, when the window is shorter than the sampling period,
+    the last sample before it and the first after it)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -64,7 +69,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -84,25 +89,40 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    @staticmethod
+    def _parse(line):
+        """(epoch seconds, sm MHz, max sm MHz, throttle reasons) of one sample, or None."""
+        import datetime
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 10:
+            return None
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            sm, mx = float(parts[2]), float(parts[3])
+        except ValueError:
+            return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        reasons = {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}
+        return ts, sm, mx, reasons
+
+    def summary(self, window=None):
+        samples = [x for x in (self._parse(ln) for ln in self.lines) if x is not None]
+        kind = "all"
+        if window is not None and samples:
+            t0, t1 = window
+            inside = [x for x in samples if t0 <= x[0] <= t1]
+            if inside:
+                samples, kind = inside, "timed"
+            else:  # the window fell between two samples: the ones around it
+                before = [x for x in samples if x[0] < t0]
+                after = [x for x in samples if x[0] > t1]
+                samples = before[-1:] + after[:1]
+                kind = "around the timed window"
+        if not samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set().union(*(x[3] for x in samples))
+        return {"sm_mhz": statistics.median(x[1] for x in samples), "sm_max_mhz": max(x[2] for x in samples),
+                "reasons": sorted(reasons), "samples": len(samples), "window": kind}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -190,28 +210,27 @@ def run_gpu(args):
     comp_edges = [int(deg[level[i] >= 0].sum().item()) // 2 for i in range(NSRC)] if only in ("all", "bfs") else [0]
     edges_per_step = (m_und if only in ("all", "tc") else 0) + sum(comp_edges) + iters * m_und
 
-    for _ in range(args.warmup):
-        step(rp, ci)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-
     marks = [[ev() for _ in range(4)] for _ in range(args.steps)]
     start, end = ev(), ev()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk:  # sampling from before the warm-up through the timed steps
+        for _ in range(args.warmup):
+            step(rp, ci)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         launches0 = L.kernel_launches()
         L.timing_reset()
         L.timing_enable(True)
+        t_window = [time.time(), 0.0]
         start.record(stream)
         for k in range(args.steps):
             step(rp, ci, marks[k])
         end.record(stream)
         torch.cuda.synchronize()
+        t_window[1] = time.time()
         L.timing_enable(False)
         launches_timed = L.kernel_launches() - launches0
+        time.sleep(2 * ClockSampler.PERIOD_MS / 1000.0)  # the first sample after the window
     ktime = {k: L.timing_read(k) for k in L.TIMED_KERNELS}
     ms_total = max_over_ranks(start.elapsed_time(end), world)
     ms_step = ms_total / args.steps
@@ -312,7 +331,7 @@ def run_gpu(args):
 
     out = None
     if rank == 0:
-        clocks = clk.summary()
+        clocks = clk.summary(tuple(t_window))
         gteps = job_throughput(edges_per_step, world, ms_step) / 1e9
         out = {
             "metric": METRIC,
