@@ -454,9 +454,9 @@ def extras(L, dev, hbm_peak):
     b = gen.rmat_batch(512, seed=SEED)
     rp = torch.from_numpy(b.rowptr).to(dev)
     ci = torch.from_numpy(b.colidx).to(dev)
+    build_dir = os.path.join(ROOT, "paper_2104_01661_gb300", "_build")  # the library's build folder
     B = L.Batch(b.voff, rp, ci, DAMPING, 20, tile=0,
-                tune_cache=os.path.join(ROOT, "gpurun_out", "batch_tune.json") if os.path.isdir(
-                    os.path.join(ROOT, "gpurun_out")) else None)
+                tune_cache=os.path.join(build_dir, "batch_tune.json") if os.path.isdir(build_dir) else None)
     ntri = torch.empty(512, dtype=torch.int64, device=dev)
     rank = torch.empty(b.n, dtype=torch.float32, device=dev)
     bb_ms = _timed(lambda: B.run(ntri, rank))
