@@ -52,14 +52,14 @@ def peaks():
 # ---------------------------------------------------------------------------------------------
 
 class ClockSampler:
-    """nvidia-smi sampling of the SM clock and the throttle reasons (every 50 ms).  Started before
+    """nvidia-smi sampling of the SM clock and the throttle reasons (every 100 ms).  Started before
     the warm-up so that it is running when the timed steps begin; summary() keeps the samples whose
     timestamps fall in the timed window (or, when the window is shorter than the sampling period,
     the last sample before it and the first after it)."""
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-    PERIOD_MS = 50
+    PERIOD_MS = 100
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
