@@ -171,8 +171,8 @@ int lagr_release_memory(uint64_t keep_bytes, char *msg);
 int lagr_graph_new(lagr_graph *G, int32_t n, int64_t nnz, const int32_t *rowptr,
                    const int32_t *colidx, const float *val, int32_t kind, char *msg);
 
-/* Free the struct and every cached property; *G is set to NULL.  Frees are
- * issued on `stream`.  A NULL *G is a no-op. */
+/* Free the struct and every cached property (LAGraph_Delete, Sec. II-A); *G
+ * is set to NULL.  Frees are issued on `stream`.  A NULL *G is a no-op. */
 int lagr_graph_free(lagr_graph *G, void *stream, char *msg);
 
 /* Drop every cached property (Sec. IV, DeleteProperties). */
@@ -290,7 +290,8 @@ int lagr_pagerank(float *rank, int32_t *iters, lagr_graph G, float damping, floa
                   int32_t itermax, const float *teleport, int32_t flags, void *stream, char *msg);
 
 /*
- * Adjoint of the weighted PageRank fixed point (the paper has no adjoint;
+ * Adjoint of the weighted PageRank fixed point of Alg. 3 (Sec. IV-C, with
+ * plus.times of Table II; the paper has no adjoint:
  * this is the implicit-function derivative of the iteration above).  For a
  * loss L with dL/drank = g, solve
  *   lambda = g + damping W lambda [+ damping (v . lambda) 1_dangling]
@@ -310,8 +311,11 @@ int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t *iters,
                            void *stream, char *msg);
 
 /*
- * Many graphs at once.  A batch is g undirected graphs concatenated
- * block-diagonally into one CSR (vertex ids shifted by voff).  A plan holds
+ * Many graphs at once: the triangle count of Alg. 6 and the PageRank of
+ * Alg. 3 for each of g graphs in one launch, against the per-call overhead
+ * the paper measures on high-diameter inputs (Sec. V-C).  A batch is g
+ * undirected graphs concatenated block-diagonally into one CSR (vertex ids
+ * shifted by voff).  A plan holds
  * the orientation, the work partition and a CUDA graph of the whole pass
  * (triangle count of every member, then `iters` PageRank iterations, GAP
  * form, of every member, the teleport of member i being (1-damping)/n_i);
@@ -330,7 +334,7 @@ int lagr_batch_run(uint64_t *ntri, float *rank, lagr_batch B, void *stream, char
 int lagr_batch_tile(int32_t *tile, lagr_batch B);
 int lagr_batch_free(lagr_batch *B, void *stream, char *msg);
 
-/* library version string */
+/* library version string (no paper counterpart; LAGraph's version query) */
 const char *lagr_version(void);
 
 /* Diagnostics: the number of CUDA kernels this library has launched since it was loaded (kernels

@@ -162,3 +162,17 @@ def test_release_memory_without_pools(lib):
     msg.value = b"stale"
     assert lib.lagr_release_memory(0, msg) == 0 and msg.value == b""
     assert lib.lagr_release_memory(1 << 40, None) == 0
+
+
+def test_every_declaration_cites_its_passage():
+    # each entry point's comment names the passage of the paper that defines it (or says there is none)
+    text = open(HEADER).read()
+    pat = re.compile(r"(/\*(?:(?!\*/).)*\*/)\s*(?:#define[^\n]*\n\s*)*((?:typedef[^;]*;\s*)*)"
+                     r"(?:[A-Za-z_][\w \*]*?)\b(lagr_[A-Za-z0-9_]+)\s*\(", re.S)
+    seen = {}
+    for m in pat.finditer(text):
+        comment = re.sub(r"\s*\n\s*\*\s*", " ", m.group(1))
+        seen[m.group(3)] = bool(re.search(r"Alg\. ?\d|Sec\. ?[IVX]|Table [IVX]|no (paper )?counterpart", comment,
+                                          re.I))
+    assert len(seen) >= 15
+    assert all(seen.values()), [k for k, v in seen.items() if not v]
