@@ -19,6 +19,9 @@ stand-ins for their shapes):
   (0, 1] per unique edge, row-normalised in float64 and stored as float32.
 * ``rmat_batch(g)``: ``g`` independent R-MAT graphs with scale ~ U{8..16} and
   edge factor ~ U{8..32}, concatenated block-diagonally.
+* ``with_pair_weights(g)``: symmetric float32 edge weights uniform in (0, 1]
+  (one counter-based draw per unordered vertex pair), for single-source
+  shortest paths on an undirected graph.
 """
 from __future__ import annotations
 
@@ -70,6 +73,8 @@ def _load():
         lib.gen_sources.restype = ctypes.c_int32
         lib.gen_splitmix64_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         lib.gen_splitmix64_draw.restype = ctypes.c_uint64
+        lib.gen_pair_weights.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]
+        lib.gen_pair_weights.restype = None
         _lib = lib
     return _lib
 
@@ -189,6 +194,16 @@ def rmat_weighted_directed(scale: int, edgefactor: int = 16, seed: int = DEFAULT
     g.meta["val64"] = w64
     g.name = f"rmat{scale}_ef{edgefactor}_dir_w"
     return g
+
+
+def with_pair_weights(g: Graph, seed: int = DEFAULT_SEED) -> Graph:
+    """g with float32 values uniform in (0, 1], equal on (i, j) and (j, i)."""
+    val = np.empty(max(g.nnz, 1), dtype=np.float32)
+    _load().gen_pair_weights(g.n, _p(g.rowptr, ctypes.c_int32), _p(g.colidx, ctypes.c_int32),
+                             (seed ^ 0x55A9) & (2**64 - 1), _p(val, ctypes.c_float))
+    out = Graph(n=g.n, rowptr=g.rowptr, colidx=g.colidx, directed=g.directed, val=val[:g.nnz].copy(),
+                name=g.name + "_w", voff=g.voff, meta=dict(g.meta))
+    return out
 
 
 def sources(g: Graph, k: int, seed: int = DEFAULT_SEED) -> np.ndarray:

@@ -220,3 +220,19 @@ int32_t gen_sources(int32_t n, const int32_t *rowptr, int32_t k, uint64_t seed, 
   }
   return found;
 }
+
+/*
+ * Symmetric edge weights uniform in (0, 1], stored as float32: the entry (i, j)
+ * of a CSR gets the value of the unordered pair {min(i,j), max(i,j)}, draw
+ * min * n + max of the stream, so A(i,j) = A(j,i) on a symmetric pattern.
+ */
+void gen_pair_weights(int32_t n, const int32_t *rowptr, const int32_t *colidx, uint64_t seed, float *out) {
+#pragma omp parallel for schedule(dynamic, 4096)
+  for (int32_t i = 0; i < n; i++) {
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+      int32_t j = colidx[e];
+      uint64_t a = (uint64_t)(i < j ? i : j), b = (uint64_t)(i < j ? j : i);
+      out[e] = (float)(1.0 - unit(draw(seed, a * (uint64_t)n + b)));
+    }
+  }
+}

@@ -1,9 +1,11 @@
 """ORACLE -- test infrastructure, not part of the product.
 
 ctypes wrapper around ``oracle.c``: a plain single-threaded C99 restatement of
-triangle counting (Alg. 6), parents BFS (Alg. 1), PageRank (Alg. 3, float64,
-GAP form plus the dangling-redistribution variant), weighted PageRank and its
-adjoint.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+triangle counting (Alg. 6, fused and with C<s(L)> kept), parents BFS (Alg. 1),
+PageRank (Alg. 4, float64, GAP form plus the dangling-redistribution variant),
+weighted PageRank and its adjoint, batched betweenness centrality (Alg. 3,
+float64), delta-stepping shortest paths (Alg. 5, float32) and FastSV connected
+components (Alg. 7).  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
 of ``bench.py`` may import this package; the CUDA library never does, and the
 two share no code.
 
@@ -64,6 +66,15 @@ def _load():
                                                 ctypes.c_double, ctypes.c_double, i32, ctypes.c_int,
                                                 f64p, f64p, f64p]
         lib.oracle_pagerank_adjoint.restype = i32
+        lib.oracle_tc_edges.argtypes = [i32, i32p, i32p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)]
+        lib.oracle_tc_edges.restype = ctypes.c_uint64
+        lib.oracle_fastsv.argtypes = [i32, i32p, i32p, i32p]
+        lib.oracle_fastsv.restype = i32
+        lib.oracle_sssp_delta.argtypes = [i32, i32p, i32p, ctypes.POINTER(ctypes.c_float), i32, ctypes.c_float,
+                                          ctypes.POINTER(ctypes.c_float)]
+        lib.oracle_sssp_delta.restype = i32
+        lib.oracle_bc.argtypes = [i32, i32p, i32p, i32, i32p, f64p]
+        lib.oracle_bc.restype = i32
         _lib = lib
     return _lib
 
@@ -107,6 +118,56 @@ def tc_sample(g, method: int = TC_AUTO, stride: int = 1):
     return int(t), int(ent.value), float(sec.value)
 
 
+def tc_edges(g, method: int = TC_AUTO):
+    """(c, t): the unfused form of Alg. 6 -- c[e] (uint32, CSR order of g) is the value of
+    C<s(L)> = L plus.pair U' at the stored entry e when e lies in L after the degree ordering
+    (0 otherwise), t = sum(c)."""
+    n, rp, prp, ci, pci = _csr(g)
+    c = np.zeros(max(g.nnz, 1), dtype=np.uint32)
+    t = _load().oracle_tc_edges(n, prp, pci, method, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    if t == 2**64 - 1:
+        raise MemoryError("oracle_tc_edges")
+    return c[:g.nnz], int(t)
+
+
+def fastsv(g):
+    """(f, rounds): connected components by Alg. 7 (FastSV); f[u] = the smallest vertex id of u's
+    component."""
+    n, rp, prp, ci, pci = _csr(g)
+    f = np.empty(max(n, 1), dtype=np.int32)
+    k = _load().oracle_fastsv(n, prp, pci, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if k < 0:
+        raise MemoryError("oracle_fastsv")
+    return f[:n], int(k)
+
+
+def sssp_delta(g, src: int, delta: float, weights=None):
+    """(t, buckets): single-source shortest paths by Alg. 5 (delta-stepping) in float32 arithmetic;
+    t[v] = +inf where v is unreachable.  weights: float32 [nnz] (default g.val)."""
+    n, rp, prp, ci, pci = _csr(g)
+    w = np.ascontiguousarray(g.val if weights is None else weights, dtype=np.float32)
+    if w.size == 0:
+        w = np.zeros(1, dtype=np.float32)
+    t = np.empty(max(n, 1), dtype=np.float32)
+    k = _load().oracle_sssp_delta(n, prp, pci, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), int(src),
+                                  float(delta), t.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    if k < 0:
+        raise ValueError("oracle_sssp_delta: bad source or delta, or out of memory")
+    return t[:n], int(k)
+
+
+def bc(g, sources):
+    """(centrality, levels): batched betweenness centrality by Alg. 3 in float64 from the given
+    sources; centrality[j] = sum over the sources s of the dependency of s on j."""
+    n, rp, prp, ci, pci = _csr(g)
+    src, psrc = _i32(np.asarray(sources, dtype=np.int32))
+    c = np.empty(max(n, 1), dtype=np.float64)
+    k = _load().oracle_bc(n, prp, pci, len(src), psrc, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if k < 0:
+        raise ValueError("oracle_bc: bad source or out of memory")
+    return c[:n], int(k)
+
+
 def tc_wants_sort(g):
     """(decision, mean, median) of the degree heuristic of Alg. 6."""
     n, rp, prp, _, _ = _csr(g)
@@ -129,7 +190,7 @@ def bfs(g, src: int):
 
 
 def pagerank(g, damping: float = 0.85, tol: float = 1e-7, itermax: int = 100, dangling: bool = False):
-    """(r, iterations, last residual) by Alg. 3 in float64 (plus.second, edge values ignored)."""
+    """(r, iterations, last residual) by Alg. 4 in float64 (plus.second, edge values ignored)."""
     n, rp, prp, ci, pci = _csr(g)
     r = np.empty(max(n, 1), dtype=np.float64)
     res = ctypes.c_double()
