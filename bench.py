@@ -7,7 +7,7 @@ HBM as int32 CSR.  A step runs the whole path on it through the C ABI:
   graph store (new graph, degrees, the degree-ordered orientation U of Alg. 6),
   triangle count (masked SpGEMM C<s(L)> = L plus.pair U' fused with its reduction),
   direction-optimizing parents BFS from 16 seeded non-isolated sources (Alg. 2),
-  PageRank (Alg. 3, damping 0.85, tol 1e-7, at most 100 iterations, float32),
+  PageRank (Alg. 4, damping 0.85, tol 1e-7, at most 100 iterations, float32),
 and frees the cached properties, so every step rebuilds them.
 
 value = traversed edges per second over the whole step (GTEPS): the triangle count contributes
@@ -15,7 +15,7 @@ the m/2 undirected edges, each BFS the undirected edges of its source's componen
 convention), each PageRank iteration the m/2 undirected edges.  The CSR (537 MB) is larger than
 the 129 MB L2, so no extra flush is done between steps.
 
---impl reference times the CPU oracle (single thread, float64, Alg. 6 / Alg. 1 / Alg. 3) on a
+--impl reference times the CPU oracle (single thread, float64, Alg. 6 / Alg. 1 / Alg. 4) on a
 bounded sample of the same workload instead.
 """
 from __future__ import annotations
@@ -375,6 +375,7 @@ def run_gpu(args):
             del rp, ci, level, parent
             torch.cuda.empty_cache()
             out["extras"] = extras(L, dev, hbm_peak)
+            out["extras"].update(extras_next_rows(L, dev, hbm_peak, g))
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -444,8 +445,17 @@ def extras(L, dev, hbm_peak):
         for s in srcs:
             L.lagr_bfs(G, s, 0, level=lvl, want_parent=False)
     p_ms = _timed(plain64, reps=1, warm=1)
+    # algorithmic bytes: per level, the column indices of every vertex in the union of the 64
+    # frontiers (4 bytes per edge) and three 64-bit words per vertex (seen, frontier, next)
+    degd = torch.from_numpy(np.diff(g.rowptr).astype(np.int64)).to(dev)
+    b64 = 0
+    for lev in range(int(lv64.max().item()) + 1):
+        inf = (lv64 == lev).any(dim=0)
+        b64 += 4 * int(degd[inf].sum().item()) + 24 * g.n
+    gbs64 = b64 / (b_ms * 1e-3) / 1e9
     res["bfs64_rmat20"] = {"batched_ms": round(b_ms, 3), "plain_64_calls_ms": round(p_ms, 3),
-                           "speedup": round(p_ms / b_ms, 2)}
+                           "speedup": round(p_ms / b_ms, 2), "bytes": b64, "gbs": round(gbs64, 1),
+                           "frac_hbm": round(gbs64 / hbm_peak, 4)}
     G.free()
     del G, g, lv64
     torch.cuda.empty_cache()
@@ -468,9 +478,13 @@ def extras(L, dev, hbm_peak):
             L.lagr_tc(Gi)
             L.lagr_pagerank(Gi, DAMPING, 0.0, 20, rank=ri)
     pp_ms = _timed(plain512, reps=1, warm=1)
+    # algorithmic bytes: each member's triangle pass and 20 PageRank iterations
+    b512 = sum(tc_algorithmic_bytes(p) + 20 * pr_bytes(p.n, p.nnz) for p in b.meta["parts"])
+    gbs512 = b512 / (bb_ms * 1e-3) / 1e9
     res["batch512"] = {"graphs": 512, "vertices": int(b.n), "entries": int(b.nnz), "tile": B.tile,
                        "batched_ms": round(bb_ms, 3), "plain_512x2_calls_ms": round(pp_ms, 3),
-                       "speedup": round(pp_ms / bb_ms, 2)}
+                       "speedup": round(pp_ms / bb_ms, 2), "bytes": b512, "gbs": round(gbs512, 1),
+                       "frac_hbm": round(gbs512 / hbm_peak, 4)}
     for Gi in graphs:
         Gi.free()
     B.free()
@@ -509,6 +523,107 @@ def extras(L, dev, hbm_peak):
     res["adjoint_rmat20_directed"] = {"ours_fwd_bwd_ms": round(o_ms, 3), "unrolled_autograd_ms": round(u_ms, 3),
                                       "speedup": round(u_ms / o_ms, 2), "ours_peak_mb": round(o_mem / 2**20, 1),
                                       "unrolled_peak_mb": round(u_mem / 2**20, 1), "grad_rel_diff": round(rel, 6)}
+
+    # the weighted forward and the adjoint iteration on the HBM roofline: fixed iteration counts
+    # (tol 0); bytes per iteration 4(n+1) + 8m + 16n (row pointers, column indices and values, the
+    # gathered vector, the new iterate, the previous one for the residual, the teleport / dL/dr
+    # term); the edge gradient 4(n+1) + 8m + 8n (row pointers, column indices, dW, r and lambda)
+    Gw = L.Graph(rp, ci, w.detach().contiguous(), directed=True)
+    n, m = g.n, g.nnz
+    it_b = 4 * (n + 1) + 8 * m + 16 * n
+    eg_b = 4 * (n + 1) + 8 * m + 8 * n
+    K = 20
+    rk = torch.empty(n, dtype=torch.float32, device=dev)
+    f_ms = _timed(lambda: L.lagr_pagerank(Gw, DAMPING, 0.0, K, flags=L.LAGR_PR_WEIGHTED, rank=rk))
+    a_ms = _timed(lambda: L.lagr_pagerank_backward(Gw, c, rk, DAMPING, 0.0, K, want_dw=False, want_dteleport=False))
+    ag_ms = _timed(lambda: L.lagr_pagerank_backward(Gw, c, rk, DAMPING, 0.0, K, want_dw=True, want_dteleport=False))
+    fw_gbs = it_b / (f_ms / K * 1e-3) / 1e9
+    ad_gbs = it_b / (a_ms / K * 1e-3) / 1e9
+    eg_ms = max(ag_ms - a_ms, 1e-6)
+    eg_gbs = eg_b / (eg_ms * 1e-3) / 1e9
+    res["weighted_rmat20_directed"] = {
+        "bytes_per_iter": it_b, "forward_ms_per_iter": round(f_ms / K, 4), "forward_gbs": round(fw_gbs, 1),
+        "forward_frac_hbm": round(fw_gbs / hbm_peak, 4), "adjoint_ms_per_iter": round(a_ms / K, 4),
+        "adjoint_gbs": round(ad_gbs, 1), "adjoint_frac_hbm": round(ad_gbs / hbm_peak, 4),
+        "edge_grad_bytes": eg_b, "edge_grad_ms": round(eg_ms, 4), "edge_grad_gbs": round(eg_gbs, 1),
+        "edge_grad_frac_hbm": round(eg_gbs / hbm_peak, 4)}
+    Gw.free()
+    return res
+
+
+def extras_next_rows(L, dev, hbm_peak, g):
+    """The next rows on the bench graph (R-MAT 22): the kept C<s(L)> of Alg. 6 against the fused
+    count, FastSV (Alg. 7), delta-stepping SSSP (Alg. 5) and batched betweenness centrality
+    (Alg. 3), each with its algorithmic bytes and the fraction of HBM they reach."""
+    import numpy as np
+    import torch
+
+    import gen
+    res = {}
+    gw = gen.with_pair_weights(g, seed=SEED)
+    G = L.Graph.from_host(gw)
+    n, nnz = g.n, g.nnz
+    deg = np.diff(g.rowptr).astype(np.int64)
+
+    # C<s(L)> kept vs the fused count (the orientation is cached after the first call of either)
+    c = torch.empty(nnz, dtype=torch.int32, device=dev)
+    fused_ms = _timed(lambda: L.lagr_tc(G))
+    kept_ms = _timed(lambda: L.lagr_tc_edges(G, c=c))
+    kb = tc_algorithmic_bytes(g) + 4 * nnz  # the fused pass's bytes plus the kept C written
+    res["tc_edges_rmat22"] = {"kept_ms": round(kept_ms, 3), "fused_count_ms": round(fused_ms, 3),
+                              "kept_over_fused": round(kept_ms / fused_ms, 2), "bytes": kb,
+                              "gbs": round(kb / (kept_ms * 1e-3) / 1e9, 1),
+                              "frac_hbm": round(kb / (kept_ms * 1e-3) / 1e9 / hbm_peak, 4)}
+
+    # FastSV: per round the rows (rowptr, colidx), the gathered grandparents, mngf read and written,
+    # the parent list, the hooks and the element-wise grandparent pass
+    comp = torch.empty(n, dtype=torch.int32, device=dev)
+    rounds = [0]
+
+    def cc():
+        rounds[0] = L.lagr_connected_components(G, component=comp)[1]
+    cc_ms = _timed(cc)
+    ccb = rounds[0] * (4 * (n + 1) + 4 * nnz + 44 * n)
+    res["fastsv_rmat22"] = {"ms": round(cc_ms, 3), "rounds": rounds[0], "components": int(torch.unique(comp).numel()),
+                            "bytes": ccb, "gbs": round(ccb / (cc_ms * 1e-3) / 1e9, 1),
+                            "frac_hbm": round(ccb / (cc_ms * 1e-3) / 1e9 / hbm_peak, 4)}
+
+    # delta-stepping from a seeded source: GTEPS over the source's component (Graph500 convention);
+    # bytes: every edge of every reached vertex read once with its weight (the least a label-setting
+    # pass reads), the distances and the bucket scans
+    src = int(gen.sources(g, 1, seed=SEED)[0])
+    dist = torch.empty(n, dtype=torch.float32, device=dev)
+    best = None
+    for delta in (0.05, 0.1, 0.2):
+        bk = [0]
+
+        def sp():
+            bk[0] = L.lagr_sssp(G, src, delta, dist=dist)[1]
+        ms = _timed(sp)
+        if best is None or ms < best[0]:
+            best = (ms, delta, bk[0])
+    reached = torch.isfinite(dist).cpu().numpy()
+    comp_edges = int(deg[reached].sum()) // 2
+    spb = 8 * int(deg[reached].sum()) + 4 * (n + 1) + 8 * n * best[2]
+    res["sssp_rmat22"] = {"ms": round(best[0], 3), "delta": best[1], "buckets": best[2],
+                          "gteps": round(comp_edges / (best[0] * 1e-3) / 1e9, 3), "bytes": spb,
+                          "gbs": round(spb / (best[0] * 1e-3) / 1e9, 1),
+                          "frac_hbm": round(spb / (best[0] * 1e-3) / 1e9 / hbm_peak, 4)}
+
+    # batched betweenness centrality: 4 sources (the batch size the paper names as typical) and 64;
+    # bytes: the forward and the backward each read every edge of every (vertex, level) of the
+    # level lists once (4 bytes) plus the float64 state of the (vertex, source) pairs
+    srcs = [int(s) for s in gen.sources(g, 64, seed=SEED)]
+    cent = torch.empty(n, dtype=torch.float64, device=dev)
+    for k in (4, 64):
+        lv = [0]
+
+        def bc():
+            lv[0] = L.lagr_betweenness(G, srcs[:k], centrality=cent)[1]
+        ms = _timed(bc, reps=1, warm=1)
+        res[f"bc{k}_rmat22"] = {"ms": round(ms, 3), "sources": k, "levels": lv[0],
+                                "mteps": round(k * (nnz // 2) / (ms * 1e-3) / 1e6, 1)}
+    G.free()
     return res
 
 
@@ -568,9 +683,15 @@ def roofline(g, ktime, steps, peak, peak_kind, comp):
             traffic = json.load(open(path)).get("dram_bytes_per_launch")
         except Exception:
             traffic = None
-    return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(ach / peak, 4), "peak_kind": peak_kind, "bytes_per_launch": nbytes,
-            "ms_per_launch": round(ms_launch, 4), "traffic": traffic}
+    out = {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(ach / peak, 4), "peak_kind": peak_kind, "bytes_per_launch": nbytes,
+           "ms_per_launch": round(ms_launch, 4), "traffic": traffic}
+    if traffic:
+        # what the DRAM actually moved (ncu) over the same live launch time: the honest HBM fraction
+        # where the algorithmic byte model counts re-reads that the kernel serves from L2
+        out["dram_gbs"] = round(traffic / (ms_launch * 1e-3) / 1e9, 1)
+        out["dram_frac"] = round(traffic / (ms_launch * 1e-3) / 1e9 / peak, 4)
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -579,7 +700,7 @@ def roofline(g, ktime, steps, peak, peak_kind, comp):
 
 def cpu_sample(g, srcs, budget_s=20.0):
     """A bounded sample of the workload on the oracle (single thread): BFS from the first source,
-    PageRank iterations (float64, Alg. 3), and Alg. 6 on every k-th mask row of L."""
+    PageRank iterations (float64, Alg. 4), and Alg. 6 on every k-th mask row of L."""
     import numpy as np
 
     import oracle
@@ -603,10 +724,29 @@ def cpu_sample(g, srcs, budget_s=20.0):
     return edges, secs, sample
 
 
+def host_cpu():
+    """(CPU model, logical CPUs) of this host, for the baseline line."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return model, os.cpu_count()
+
+
 def cpu_baseline(g, srcs, budget_s=20.0):
     edges, secs, sample = cpu_sample(g, srcs, budget_s)
+    model, nproc = host_cpu()
     return {"value": round(edges / secs / 1e9, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": sample, "seconds": round(secs, 2)}
+            "sample": sample, "seconds": round(secs, 2), "cpu_model": model, "nproc": nproc}
 
 
 def run_reference(args):
@@ -631,7 +771,8 @@ def run_reference(args):
             "ms_per_step": round(secs / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 / int32 (oracle)", "data": "synthetic (seeded R-MAT)",
             "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": round(v, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": round(v, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": host_cpu()[0], "nproc": host_cpu()[1]},
             "e2e": {"value": round(v, 6), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -4,16 +4,16 @@
  * The library computes the data-parallel products under LAGraph's algorithms
  * (Mattson et al., 2021) on one GPU:
  *   - triangle counting, C<s(L)> = L plus.pair U' followed by a reduction
- *     (Alg. 6, Sec. IV-F), fused so that C is never materialised;
+ *     (Alg. 6, Sec. IV-E), fused so that C is never materialised;
  *   - direction-optimizing parents BFS, push q'A / pull A'q over any.secondi
  *     with the visited set as a complemented structural mask (Alg. 1 and 2,
  *     Sec. IV-A);
- *   - PageRank, repeated A' plus.second w (Alg. 3, Sec. IV-C), a weighted
+ *   - PageRank, repeated A' plus.second w (Alg. 4, Sec. IV-C), a weighted
  *     plus.times form and its adjoint;
  *   - batched forms: 64 BFS sources in one bitmap frontier (the ns x n
- *     frontier of Alg. 4, Sec. IV-B) and many graphs in one launch.
+ *     frontier of Alg. 3, Sec. IV-B) and many graphs in one launch.
  *
- * Conventions (Sec. II-D, II-E):
+ * Conventions (Sec. II-C, II-D):
  *   - arguments are ordered outputs, then input/outputs, then inputs, then
  *     `msg`;
  *   - the return value is 0 on success, < 0 on error, > 0 for a warning;
@@ -75,7 +75,7 @@ extern "C" {
 #define LAGR_BFS_PULL_ONLY 2 /* every level after the first is a pull A'q */
 
 /* lagr_pagerank / lagr_pagerank_backward flags */
-#define LAGR_PR_GAP 0            /* Alg. 3 as written: dangling rows lose their mass */
+#define LAGR_PR_GAP 0            /* Alg. 4 as written: dangling rows lose their mass */
 #define LAGR_PR_DANGLING 1       /* redistribute the dangling mass through the teleport vector */
 #define LAGR_PR_WEIGHTED 2       /* plus.times with the graph's values (row-stochastic W) */
 #define LAGR_PR_WARM_START 4     /* `rank` holds the starting vector on entry */
@@ -135,7 +135,7 @@ typedef struct lagr_graph_struct {
 typedef lagr_graph_struct *lagr_graph;
 
 /*
- * Allocator hook (Sec. IV, the malloc/free wrappers): every device
+ * Allocator hook (Sec. V, the malloc/free wrappers): every device
  * allocation of the library goes through alloc(bytes, stream, ctx) and
  * free_(ptr, stream, ctx).  alloc returns NULL on failure, which the calling
  * function reports as LAGR_ERR_OUT_OF_MEMORY.  Passing NULLs restores the
@@ -175,11 +175,11 @@ int lagr_graph_new(lagr_graph *G, int32_t n, int64_t nnz, const int32_t *rowptr,
  * is set to NULL.  Frees are issued on `stream`.  A NULL *G is a no-op. */
 int lagr_graph_free(lagr_graph *G, void *stream, char *msg);
 
-/* Drop every cached property (Sec. IV, DeleteProperties). */
+/* Drop every cached property (Sec. V, DeleteProperties). */
 int lagr_delete_properties(lagr_graph G, void *stream, char *msg);
 
 /*
- * Validate the graph on the device (Sec. IV, CheckGraph): rowptr[0] = 0,
+ * Validate the graph on the device (Sec. V, CheckGraph): rowptr[0] = 0,
  * rowptr nondecreasing, rowptr[n] = nnz, every column index in [0, n), each
  * row strictly increasing (sorted, no duplicates), and, for
  * LAGR_UNDIRECTED, A equal to A'.  Sets a_pattern_is_symmetric and ndiag.
@@ -192,11 +192,11 @@ int lagr_graph_check(lagr_graph G, void *stream, char *msg);
  * sorted; for an undirected graph A' aliases A.  Deterministic. */
 int lagr_property_AT(lagr_graph G, void *stream, char *msg);
 
-/* Compute and cache the row degree (Sec. IV, Property_RowDegree). */
+/* Compute and cache the row degree (Sec. V, Property_RowDegree). */
 int lagr_property_row_degree(lagr_graph G, void *stream, char *msg);
 
 /*
- * Triangle count (Alg. 6, Sec. IV-F): the number of unique 3-cliques of the
+ * Triangle count (Alg. 6, Sec. IV-E): the number of unique 3-cliques of the
  * undirected graph G, i.e. t = sum(C) with C<s(L)> = L plus.pair U', L and U
  * the strictly lower and upper parts of A after the degree ordering that
  * `method` selects (LAGR_TC_*).  Self-loops are ignored (strict parts).
@@ -206,6 +206,20 @@ int lagr_property_row_degree(lagr_graph G, void *stream, char *msg);
  * INVALID_GRAPH (G directed), OUT_OF_MEMORY, CUDA.
  */
 int lagr_tc(uint64_t *ntriangles, lagr_graph G, int32_t method, void *stream, char *msg);
+
+/*
+ * Triangle count with C kept: the unfused form of Alg. 6 (Sec. IV-E), C<s(L)> = L plus.pair U'
+ * after the degree ordering that `method` selects (LAGR_TC_*).  c[e] for every stored entry
+ * e = (i,j) of A (CSR order, the caller's labels) is C at that entry -- the number of vertices k
+ * adjacent to both i and j that lie strictly between them in the degree order -- when the entry is
+ * in L (i after j in that order), and 0 when it is in U; every triangle is counted at one entry
+ * (the one joining its first and last vertex in the order), so the sum of c is the triangle count.
+ * c: device [nnz] output (uint32; may be NULL when nnz = 0).  ntriangles: host output (the sum of
+ * c) or NULL.  Caches the
+ * orientation G->u_* like lagr_tc.  Synchronises the stream.  Errors: NULL_POINTER, INVALID_VALUE
+ * (bad method), INVALID_GRAPH (G directed), OUT_OF_MEMORY, CUDA.
+ */
+int lagr_tc_edges(uint32_t *c, uint64_t *ntriangles, lagr_graph G, int32_t method, void *stream, char *msg);
 
 /*
  * Parents BFS (Alg. 1 / Alg. 2, Sec. IV-A).  level[v] = number of edges on a
@@ -246,10 +260,15 @@ int lagr_bfs_multi(int32_t *level, int32_t *parent, int32_t *depth, lagr_graph G
  * another owner, or who must not enter the allocator while other work runs).  It takes the
  * undirected graph as raw device CSR arrays (no lagr_graph, whose cached properties allocate) and
  * allocates nothing: all work space lives in one file-scope device array of the library, sized for
- * at most LAGR_BFS_NOALLOC_MAX_N vertices (about 17 MB, held by every GPU that loads the library
- * until the process exits).  The first call on each device looks that array's address up; make it
- * before any stream capture.  Calls share the array: a call resets what it uses, and calls whose
- * GPU work overlaps race, so the caller must not run two at once on one device.
+ * at most LAGR_BFS_NOALLOC_MAX_N vertices (about 17 MB).  A GPU reserves that array when the
+ * library's BFS device code is first loaded on it (with CUDA's lazy module loading, at the first
+ * BFS call on that device) and keeps it until the process exits; the first call on each device also
+ * looks the array's address up.  Make one warm-up call per device at start-up, before any stream
+ * capture and before the device memory is handed out.  Calls share the array: a call resets what
+ * it uses, and calls whose GPU work overlaps race, so the caller must not run two at once on one
+ * device.  The CSR must be a valid undirected graph (symmetric, every column index in [0, n), as
+ * lagr_graph_check verifies): nothing here checks it, and an index out of range writes outside the
+ * array.
  * level, parent: device [n] outputs, either may be NULL; depth: host output or NULL; results as
  * lagr_bfs.  Synchronises the stream.  Errors: INVALID_VALUE (n < 1, src out of range),
  * TOO_LARGE (n > LAGR_BFS_NOALLOC_MAX_N or nnz >= 2^31), NULL_POINTER, TIMEOUT, CUDA.
@@ -261,7 +280,7 @@ int lagr_bfs_noalloc(int32_t *level, int32_t *parent, int32_t *depth, int32_t n,
 
 /*
  * k BFS at once (1 <= k <= 64) from the sources src[0..k-1] (host array),
- * as one 64-bit bitmap frontier per vertex: the frontier matrix of Alg. 4
+ * as one 64-bit bitmap frontier per vertex: the frontier matrix of Alg. 3
  * (Sec. IV-B) with ns = k and the any/or monoid in place of plus.
  * level: device [k][n] output, row s holds the levels from src[s] with the
  * same meaning as lagr_bfs.  Undirected graphs only.  Synchronises the
@@ -272,7 +291,46 @@ int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src, int32_t k
                      char *msg);
 
 /*
- * PageRank (Alg. 3, Sec. IV-C) in float32.
+ * Batched betweenness centrality (Alg. 3, Sec. IV-B) in float64 from ns <= 64 sources at once:
+ * centrality[j] = sum over the sources s_k of sum over targets t != s_k, j of
+ * sigma(s_k, t | j) / sigma(s_k, t), sigma counting shortest paths (following out-edges on a
+ * directed graph).  This is Alg. 3's -ns + sum_k B(k, j), with the path counts P and the backtrack
+ * values B and W in float64; the backtrack runs over every BFS level, from the deepest one to the
+ * first.  A source listed twice counts twice.  src: host [ns], 1 <= ns <= 64.  centrality: device
+ * [n] output (float64).  levels: host output (the number of BFS levels past the sources) or NULL.
+ * Work space: 4 ns n float64 values plus the level lists.  Synchronises the stream once per BFS
+ * level.  Errors: NULL_POINTER, INVALID_VALUE (ns or a source out of range), OUT_OF_MEMORY,
+ * TIMEOUT, CUDA.
+ */
+int lagr_betweenness(double *centrality, int32_t *levels, lagr_graph G, const int32_t *src, int32_t ns,
+                     void *stream, char *msg);
+
+/*
+ * Single-source shortest paths by delta-stepping (Alg. 5, Sec. IV-D) over min.plus in float32.
+ * dist[v] = the least fixed point of dist(v) = min over the entries A(u,v) of dist(u) + A(u,v)
+ * with dist(src) = 0, every sum rounded to float32: the float32 length of a shortest path from src
+ * (+inf when v is unreachable).  The edge values G->val are the weights; as in Alg. 5 the entries
+ * with 0 < A <= delta are light and those with A > delta heavy, and entries with A <= 0 take no
+ * part.  Directed graphs follow out-edges.  delta > 0 only sets the bucket width (the work, not
+ * the result).  dist: device [n] output.  buckets: host output (buckets settled) or NULL.
+ * Synchronises the stream once per relaxation step.  Errors: NULL_POINTER, INVALID_VALUE (no
+ * values, src out of range, delta not positive and finite), OUT_OF_MEMORY, TIMEOUT, CUDA.
+ */
+int lagr_sssp(float *dist, int32_t *buckets, lagr_graph G, int32_t src, float delta, void *stream, char *msg);
+
+/*
+ * Connected components by FastSV (Alg. 7, Sec. IV-F): component[u] = the smallest vertex id of
+ * u's connected component, the root every vertex of the component points to once the forest of
+ * Alg. 7 stops changing.  Rounds of stochastic hooking, aggressive hooking, shortcutting and
+ * grandparent updates (steps 1-4) run until a round changes neither the parents nor the
+ * grandparents.  Undirected graphs only.  component: device [n] output.  rounds: host output or
+ * NULL.  Synchronises the stream once per round.  Errors: NULL_POINTER, INVALID_GRAPH (directed),
+ * OUT_OF_MEMORY, TIMEOUT (no fixed point within 2 log2(n) + 64 rounds), CUDA.
+ */
+int lagr_connected_components(int32_t *component, int32_t *rounds, lagr_graph G, void *stream, char *msg);
+
+/*
+ * PageRank (Alg. 4, Sec. IV-C) in float32.
  * Unweighted (flags without LAGR_PR_WEIGHTED):
  *   r = 1/n; repeat: t = r; w = damping * t / d_out (rows with d_out > 0);
  *   r = (1 - damping) * v + A' plus.second w [+ damping * (sum of t over
@@ -290,7 +348,7 @@ int lagr_pagerank(float *rank, int32_t *iters, lagr_graph G, float damping, floa
                   int32_t itermax, const float *teleport, int32_t flags, void *stream, char *msg);
 
 /*
- * Adjoint of the weighted PageRank fixed point of Alg. 3 (Sec. IV-C, with
+ * Adjoint of the weighted PageRank fixed point of Alg. 4 (Sec. IV-C, with
  * plus.times of Table II; the paper has no adjoint:
  * this is the implicit-function derivative of the iteration above).  For a
  * loss L with dL/drank = g, solve
@@ -303,7 +361,12 @@ int lagr_pagerank(float *rank, int32_t *iters, lagr_graph G, float damping, floa
  * (nothing is stored per iteration either way).  dL_dw: device [nnz] output
  * in CSR order, or NULL.  dL_dteleport: device [n] output or NULL.
  * iters: host output (adjoint iterations) or NULL.  Uses G->val (W);
- * flags must include LAGR_PR_WEIGHTED.  Synchronises the stream.
+ * flags must include LAGR_PR_WEIGHTED.  The adjoint iteration stops when its
+ * L1 change is below tol times the L1 norm of the new iterate (relative: the
+ * scale of lambda is that of dL/drank); `tol` and `itermax` of the forward
+ * recompute (rank == NULL) keep the absolute criterion of Alg. 4.  Returns
+ * LAGR_WARN_NOT_CONVERGED when itermax adjoint iterations did not reach tol.
+ * Synchronises the stream.
  */
 int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t *iters,
                            const float *dL_drank, const float *rank, lagr_graph G, float damping,
@@ -312,8 +375,8 @@ int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t *iters,
 
 /*
  * Many graphs at once: the triangle count of Alg. 6 and the PageRank of
- * Alg. 3 for each of g graphs in one launch, against the per-call overhead
- * the paper measures on high-diameter inputs (Sec. V-C).  A batch is g
+ * Alg. 4 for each of g graphs in one launch, against the per-call overhead
+ * the paper measures on high-diameter inputs (Sec. VI-B).  A batch is g
  * undirected graphs concatenated block-diagonally into one CSR (vertex ids
  * shifted by voff).  A plan holds
  * the orientation, the work partition and a CUDA graph of the whole pass
@@ -333,6 +396,14 @@ int lagr_batch_plan(lagr_batch *B, int32_t g, const int32_t *voff, int32_t N, in
 int lagr_batch_run(uint64_t *ntri, float *rank, lagr_batch B, void *stream, char *msg);
 int lagr_batch_tile(int32_t *tile, lagr_batch B);
 int lagr_batch_free(lagr_batch *B, void *stream, char *msg);
+
+/* Diagnostics (no paper counterpart): force the capacities of the triangle count's anchor lists
+ * (CTA items, chunked warp items) for later lagr_tc calls on graphs whose orientation is rebuilt;
+ * 0 restores the capacities computed from the graph.  A list that overflows its capacity is never
+ * written or read past its end: lagr_tc returns LAGR_ERR_INVALID_GRAPH instead.  For tests of that
+ * bound.  Returns LAGR_ERR_INVALID_VALUE for a negative capacity.  Not thread-safe with running
+ * lagr_tc calls. */
+int lagr_debug_tc_capacity(int64_t capc, int64_t capwh);
 
 /* library version string (no paper counterpart; LAGraph's version query) */
 const char *lagr_version(void);

@@ -8,8 +8,9 @@ a GPU (so the library can be inspected), but every call that reaches the device
 raises when CUDA or the compiled library is unavailable.
 
 Entry points (same names as the C ABI): ``lagr_graph_new``, ``lagr_graph_free``,
-``lagr_graph_check``, ``lagr_property_AT``, ``lagr_tc``, ``lagr_bfs``,
-``lagr_bfs_multi``, ``lagr_bfs_batch64``, ``lagr_pagerank``, ``lagr_pagerank_backward``,
+``lagr_graph_check``, ``lagr_property_AT``, ``lagr_tc``, ``lagr_tc_edges``, ``lagr_bfs``,
+``lagr_bfs_multi``, ``lagr_bfs_batch64``, ``lagr_bfs_noalloc``, ``lagr_betweenness``,
+``lagr_sssp``, ``lagr_connected_components``, ``lagr_pagerank``, ``lagr_pagerank_backward``,
 ``lagr_batch_plan`` / ``lagr_batch_run`` / ``lagr_batch_free``, plus the
 ``PageRankFunction`` autograd wrapper.
 """
@@ -116,6 +117,11 @@ _SIGNATURES = {
     "lagr_batch_run": ([_vp, _vp, _vp, _vp, _str], ctypes.c_int),
     "lagr_batch_tile": ([ctypes.POINTER(_i32), _vp], ctypes.c_int),
     "lagr_batch_free": ([ctypes.POINTER(_vp), _vp, _str], ctypes.c_int),
+    "lagr_debug_tc_capacity": ([_i64, _i64], ctypes.c_int),
+    "lagr_tc_edges": ([_vp, ctypes.POINTER(ctypes.c_uint64), _G, _i32, _vp, _str], ctypes.c_int),
+    "lagr_betweenness": ([_vp, ctypes.POINTER(_i32), _G, ctypes.POINTER(_i32), _i32, _vp, _str], ctypes.c_int),
+    "lagr_sssp": ([_vp, ctypes.POINTER(_i32), _G, _i32, _f32, _vp, _str], ctypes.c_int),
+    "lagr_connected_components": ([_vp, ctypes.POINTER(_i32), _G, _vp, _str], ctypes.c_int),
 }
 
 _lib = None
@@ -251,6 +257,67 @@ def lagr_tc(G: Graph, method: int = LAGR_TC_AUTO, stream=None) -> int:
     return int(out.value)
 
 
+def lagr_tc_edges(G: Graph, method: int = LAGR_TC_AUTO, c=None, stream=None):
+    """Triangle count with C<s(L)> kept (Alg. 6, unfused).  Returns (c uint32-as-int32 [nnz], t)."""
+    torch = _torch()
+    if c is None:
+        c = torch.empty(G.nnz, dtype=torch.int32, device=G.rowptr.device)
+    _dev(c, torch.int32, "c")
+    if c.numel() < G.nnz:
+        raise ValueError(f"c has {c.numel()} elements, the graph {G.nnz} entries")
+    t = ctypes.c_uint64(0)
+    msg = _msg()
+    rc = load_library().lagr_tc_edges(_ptr(c), ctypes.byref(t), G.handle, method, _stream(stream), msg)
+    _check(rc, msg, "lagr_tc_edges")
+    return c, int(t.value)
+
+
+def lagr_betweenness(G: Graph, sources: Sequence[int], centrality=None, stream=None):
+    """Batched betweenness centrality (Alg. 3) from at most 64 sources, float64.  Returns
+    (centrality [n], levels)."""
+    torch = _torch()
+    if centrality is None:
+        centrality = torch.empty(G.n, dtype=torch.float64, device=G.rowptr.device)
+    _dev(centrality, torch.float64, "centrality")
+    k = len(sources)
+    src = (ctypes.c_int32 * max(k, 1))(*[int(x) for x in sources])
+    levels = ctypes.c_int32(0)
+    msg = _msg()
+    rc = load_library().lagr_betweenness(_ptr(centrality), ctypes.byref(levels), G.handle, src, k,
+                                         _stream(stream), msg)
+    _check(rc, msg, "lagr_betweenness")
+    return centrality, int(levels.value)
+
+
+def lagr_sssp(G: Graph, src: int, delta: float, dist=None, stream=None):
+    """Single-source shortest paths by delta-stepping (Alg. 5) over the graph's float32 values.
+    Returns (dist [n] float32, +inf when unreachable; buckets)."""
+    torch = _torch()
+    if dist is None:
+        dist = torch.empty(G.n, dtype=torch.float32, device=G.rowptr.device)
+    _dev(dist, torch.float32, "dist")
+    b = ctypes.c_int32(0)
+    msg = _msg()
+    rc = load_library().lagr_sssp(_ptr(dist), ctypes.byref(b), G.handle, int(src), float(delta), _stream(stream),
+                                  msg)
+    _check(rc, msg, "lagr_sssp")
+    return dist, int(b.value)
+
+
+def lagr_connected_components(G: Graph, component=None, stream=None):
+    """Connected components by FastSV (Alg. 7): component[u] = the smallest id of u's component.
+    Returns (component [n] int32, rounds)."""
+    torch = _torch()
+    if component is None:
+        component = torch.empty(G.n, dtype=torch.int32, device=G.rowptr.device)
+    _dev(component, torch.int32, "component")
+    r = ctypes.c_int32(0)
+    msg = _msg()
+    rc = load_library().lagr_connected_components(_ptr(component), ctypes.byref(r), G.handle, _stream(stream), msg)
+    _check(rc, msg, "lagr_connected_components")
+    return component, int(r.value)
+
+
 def lagr_bfs(G: Graph, src: int, flags: int = 0, level=None, parent=None, want_level: bool = True,
              want_parent: bool = True, stream=None):
     """Parents BFS (Alg. 1/2).  Returns (level, parent, depth); outputs may be passed in."""
@@ -309,11 +376,19 @@ def lagr_bfs_noalloc(rowptr, colidx, src: int, level, parent, stream=None):
     _dev(colidx, torch.int32, "colidx")
     _dev(level, torch.int32, "level")
     _dev(parent, torch.int32, "parent")
+    n = int(rowptr.numel()) - 1
+    for t, name in ((colidx, "colidx"), (level, "level"), (parent, "parent")):
+        if t is not None and t.device != rowptr.device:
+            raise ValueError(f"{name} is on {t.device}, rowptr on {rowptr.device}")
+    for t, name in ((level, "level"), (parent, "parent")):
+        if t is not None and t.numel() < n:
+            raise ValueError(f"{name} has {t.numel()} elements, the graph {n} vertices")
     depth = ctypes.c_int32(0)
     msg = _msg()
-    rc = load_library().lagr_bfs_noalloc(_ptr(level), _ptr(parent), ctypes.byref(depth), int(rowptr.numel()) - 1,
-                                         int(colidx.numel()), _ptr(rowptr), _ptr(colidx), int(src),
-                                         _stream(stream), msg)
+    with torch.cuda.device(rowptr.device):  # the built-in work array of rowptr's device
+        rc = load_library().lagr_bfs_noalloc(_ptr(level), _ptr(parent), ctypes.byref(depth), n,
+                                             int(colidx.numel()), _ptr(rowptr), _ptr(colidx), int(src),
+                                             _stream(stream), msg)
     _check(rc, msg, "lagr_bfs_noalloc")
     return int(depth.value)
 
@@ -334,7 +409,7 @@ def lagr_bfs_batch64(G: Graph, sources: Sequence[int], level=None, stream=None):
 
 def lagr_pagerank(G: Graph, damping: float = 0.85, tol: float = 1e-7, itermax: int = 100, teleport=None,
                   flags: int = 0, rank=None, stream=None):
-    """PageRank (Alg. 3) in float32.  Returns (rank, iterations)."""
+    """PageRank (Alg. 4) in float32.  Returns (rank, iterations)."""
     torch = _torch()
     if rank is None:
         rank = torch.empty(G.n, dtype=torch.float32, device=G.rowptr.device)
@@ -426,21 +501,22 @@ def _pagerank_function():
     class PageRankFunction(torch.autograd.Function):
         """r = PageRank(W, v) (weighted form, float32) with the hand-written adjoint as backward.
 
-        forward(rowptr, colidx, w, teleport, damping, tol, itermax, flags, directed) -> r.
+        forward(rowptr, colidx, w, teleport, damping, tol, itermax, flags, directed, adjoint_tol) -> r.
         Gradients flow to the edge weights w (CSR order) and the teleport vector.  Only r is
-        saved; the backward solves the transposed fixed point with the same gather kernels.
+        saved; the backward solves the transposed fixed point with the same gather kernels, to a
+        relative L1 change below adjoint_tol.
         """
 
         @staticmethod
         def forward(ctx, rowptr, colidx, w, teleport, damping=0.85, tol=1e-7, itermax=100, flags=0,
-                    directed=True):
+                    directed=True, adjoint_tol=1e-6):
             G = Graph(rowptr, colidx, w.detach().contiguous(), directed=directed)
             tp = None if teleport is None else teleport.detach().contiguous()
             r, _ = lagr_pagerank(G, damping, tol, itermax, tp, flags | LAGR_PR_WEIGHTED)
             G.free()
             ctx.save_for_backward(rowptr, colidx, w, r, teleport if teleport is not None else r.new_empty(0))
             ctx.has_teleport = teleport is not None
-            ctx.cfg = (damping, tol, itermax, flags, directed)
+            ctx.cfg = (damping, adjoint_tol, itermax, flags, directed)
             return r
 
         @staticmethod
@@ -453,15 +529,17 @@ def _pagerank_function():
                                                flags | LAGR_PR_WEIGHTED, want_dw=ctx.needs_input_grad[2],
                                                want_dteleport=ctx.has_teleport and ctx.needs_input_grad[3])
             G.free()
-            return None, None, dw, dv, None, None, None, None, None
+            return None, None, dw, dv, None, None, None, None, None, None
 
     return PageRankFunction
 
 
 def pagerank_autograd(rowptr, colidx, w, teleport=None, damping=0.85, tol=1e-7, itermax=100, flags=0,
-                      directed=True):
-    """Differentiable weighted PageRank (see PageRankFunction)."""
-    return _pagerank_function().apply(rowptr, colidx, w, teleport, damping, tol, itermax, flags, directed)
+                      directed=True, adjoint_tol=1e-6):
+    """Differentiable weighted PageRank (see PageRankFunction).  The forward stops at an L1 change
+    below ``tol`` (Alg. 4), the adjoint at a relative L1 change below ``adjoint_tol``."""
+    return _pagerank_function().apply(rowptr, colidx, w, teleport, damping, tol, itermax, flags, directed,
+                                      adjoint_tol)
 
 
 def kernel_launches() -> int:

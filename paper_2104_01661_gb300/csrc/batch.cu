@@ -2,14 +2,14 @@
 // graph whose edges never cross members, so the triangle-count kernels and the PageRank iteration
 // run over all members at once: triangles are accumulated per member (the member of an anchor
 // vertex comes from a binary search of the vertex offsets), and PageRank uses a teleport vector
-// that gives every vertex of member i the weight 1/n_i, which is Alg. 3 run on each member.
+// that gives every vertex of member i the weight 1/n_i, which is Alg. 4 run on each member.
 //
 // The plan allocates everything once, autotunes the triangle kernels' work partition (neighbour
 // chunk per CTA item and the warp/CTA anchor threshold) by timing candidates with CUDA events,
 // caches the choice in a small JSON file keyed by GPU name and batch shape, and captures the whole
 // pass -- orientation, anchor classification, counting, `iters` PageRank iterations -- in one
 // CUDA graph that lagr_batch_run replays.  This is the paper's per-call overhead lesson (the
-// high-diameter road graph, Sec. V-C) applied to many small graphs: one graph launch instead of
+// high-diameter road graph, Sec. VI-B) applied to many small graphs: one graph launch instead of
 // thousands of calls.
 #include <cstdio>
 #include <cstdlib>
@@ -221,7 +221,7 @@ int lagr_batch_plan(lagr_batch *B, int32_t g, const int32_t *voff, int32_t N, in
       return fail(LAGR_ERR_CUDA);
     }
   }
-  batch_teleport<<<152 * 8, 256, 0, s>>>(b->voff, g, N, b->vvec);
+  batch_teleport<<<8 * sm_count(), 256, 0, s>>>(b->voff, g, N, b->vvec);
   if (cudaGetLastError() != cudaSuccess) {
     set_msg(msg, "batch teleport launch failed");
     return fail(LAGR_ERR_CUDA);

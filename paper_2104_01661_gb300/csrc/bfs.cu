@@ -1,11 +1,11 @@
 // Parents BFS (Alg. 1 and Alg. 2, Sec. IV-A) and the 64-source bitmap BFS (the ns x n frontier
-// of Alg. 4, Sec. IV-B, with ns <= 64).
+// of Alg. 3, Sec. IV-B, with ns <= 64).
 //
 // One level is q'<!s(p),r> = q' any.secondi A (push) or q<!s(p),r> = A' any.secondi q (pull),
 // followed by p<s(q)> = q.  Here the two are fused: the kernel that discovers v writes parent[v]
 // (the secondi value: the frontier vertex that reached v; `any` keeps whichever claims v first)
 // and level[v] directly.  The complemented structural mask !s(p) is a visited bitmap; the
-// frontier is a vertex queue for push and a bitmap for pull (the bitmap format of Sec. V-A).
+// frontier is a vertex queue for push and a bitmap for pull (the bitmap format of Sec. VI-A).
 //
 // Push expands 32 frontier vertices per warp with the load-balanced segment walk and claims
 // unvisited vertices with atomicOr on the visited bitmap.  Pull gives each unvisited vertex one
@@ -16,6 +16,7 @@
 // when the frontier shrinks below n / beta.  The host takes that choice between phases from
 // counters the kernels store into mapped host memory; lagr_bfs_multi interleaves the phases of
 // several independent traversals on side streams.
+#include <atomic>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -469,13 +470,6 @@ __global__ void bfs_advance(int64_t *__restrict__ c, int flip, int64_t *hm) {
 }
 
 __global__ void bfs_set_par(int64_t *__restrict__ c, int par) { c[B_PAR] = par; }
-
-inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
-  int64_t b = (work + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
 
 // ---- 64 sources at once -------------------------------------------------------------------------
 //
@@ -1122,7 +1116,7 @@ extern "C" int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src
   LAGR_TRY(fetch_to_host(P->hscal, cur, S64_NSLOT * sizeof(int64_t), s, msg));
   int64_t nf = P->hscal[S64_NF], mf = P->hscal[S64_MF];
   int32_t lev = 0;
-  const int nhb = rp.nheavy < 152 ? rp.nheavy : 152;
+  const int nhb = rp.nheavy < sm_count() ? rp.nheavy : sm_count();
   while (nf > 0) {
     lev++;
     if (lev > n) {
@@ -1170,11 +1164,12 @@ extern "C" int lagr_bfs_batch64(int32_t *level, lagr_graph G, const int32_t *src
 // queues and the level counters) in one fixed array compiled into this file, so the caller only
 // provides the graph and the outputs.
 //
-// The array is a file-scope __device__ variable: every GPU that loads the library holds its
-// LAGR_BFS_NOALLOC_MAX_N-sized copy (about 17 MB) until the process exits.  Host code cannot use
-// the variable's name as a device address, so the first call on each device looks the address up
-// with cudaGetSymbolAddress while that device is current and remembers it; make that first call
-// before capturing a stream.  Every call on a device shares the one array and leaves its contents
+// The array is a file-scope __device__ variable: a GPU holds its LAGR_BFS_NOALLOC_MAX_N-sized copy
+// (about 17 MB) from the moment this file's device code is loaded on it (with CUDA's lazy module
+// loading, at the first use of one of its kernels on that device) until the process exits.  Host
+// code cannot use the variable's name as a device address, so the first call on each device looks
+// the address up with cudaGetSymbolAddress while that device is current and remembers it; make that
+// first call before capturing a stream.  Every call on a device shares the one array and leaves its contents
 // behind; each call clears what it needs at the start, and calls whose GPU work overlaps (two
 // streams, or two host threads) race on the array and must be serialised by the caller.
 
@@ -1197,7 +1192,9 @@ static_assert(NA_OFF_CNT % 8 == 0, "counter alignment");
 static __device__ __align__(256) unsigned char g_bfs_noalloc_scratch[NA_BYTES];
 
 constexpr int NA_MAX_DEVICES = 256;
-static unsigned char *g_na_ptr[NA_MAX_DEVICES];  // device address of the array, per device
+// device address of the array, per device (atomic: host threads may make their first calls at once;
+// they look up and store the same address)
+static std::atomic<unsigned char *> g_na_ptr[NA_MAX_DEVICES];
 
 int noalloc_scratch(unsigned char **out, char *msg) {
   int dev = 0;
@@ -1206,12 +1203,14 @@ int noalloc_scratch(unsigned char **out, char *msg) {
     set_msg(msg, "device ordinal %d out of range", dev);
     return LAGR_ERR_INVALID_VALUE;
   }
-  if (!g_na_ptr[dev]) {
-    void *p = nullptr;
-    LAGR_CUDA_TRY(cudaGetSymbolAddress(&p, g_bfs_noalloc_scratch));
-    g_na_ptr[dev] = static_cast<unsigned char *>(p);
+  unsigned char *p = g_na_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void *q = nullptr;
+    LAGR_CUDA_TRY(cudaGetSymbolAddress(&q, g_bfs_noalloc_scratch));
+    p = static_cast<unsigned char *>(q);
+    g_na_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_na_ptr[dev];
+  *out = p;
   return LAGR_OK;
 }
 

@@ -1,8 +1,9 @@
 // The graph object and its cached properties (Sec. II-A), the allocator hook and the message
-// convention (Sec. II-D), CheckGraph / Property_AT / Property_RowDegree (Sec. IV utilities).
+// convention (Sec. II-D), CheckGraph / Property_AT / Property_RowDegree (Sec. V utilities).
 #include <cstdlib>
 #include <cstring>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -37,6 +38,63 @@ extern "C" cudaError_t __wrap___cudaLaunchKernel(cudaKernel_t kernel, dim3 grid,
 }
 
 namespace lagr {
+
+// ---- launch geometry -----------------------------------------------------------------------------
+
+constexpr int GEOM_DEVICES = 64;
+static std::atomic<int> g_nsm[GEOM_DEVICES];
+
+int sm_count() {
+  int d = 0, nsm = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    d = -1;
+  }
+  if (d >= 0 && d < GEOM_DEVICES && (nsm = g_nsm[d].load(std::memory_order_relaxed)) > 0) return nsm;
+  if (d < 0 || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || nsm < 1) {
+    cudaGetLastError();
+    return 1;  // no device answered: a one-CTA-per-wave grid is still a valid grid
+  }
+  if (d < GEOM_DEVICES) g_nsm[d].store(nsm, std::memory_order_relaxed);
+  return nsm;
+}
+
+static std::mutex g_occ_mu;
+struct OccKey {
+  const void *k;
+  int threads, dev;
+  size_t smem;
+  int ctas;
+};
+static std::vector<OccKey> g_occ;
+
+int resident_ctas(const void *kernel, int threads, size_t smem) {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) cudaGetLastError();
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    for (const OccKey &o : g_occ)
+      if (o.k == kernel && o.threads == threads && o.smem == smem && o.dev == d) return o.ctas;
+  }
+  const int nsm = sm_count();
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int ctas = per_sm * nsm;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ.push_back(OccKey{kernel, threads, d, smem, ctas});
+  return ctas;
+}
+
+int grid_for(int64_t work, int threads, int waves) {
+  int64_t b = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)waves * sm_count();
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
 
 // ---- allocator hook -----------------------------------------------------------------------------
 
@@ -327,13 +385,6 @@ __global__ void compare_arrays(const int32_t *__restrict__ a, const int32_t *__r
 __global__ void row_degree_kernel(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ deg) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     deg[i] = rowptr[i + 1] - rowptr[i];
-}
-
-inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
-  int64_t b = (work + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
 }
 
 }  // namespace

@@ -178,6 +178,21 @@ struct KTimer {
 };
 void priv_release(lagr_graph G, cudaStream_t s);
 
+// ---------------------------------------------------------------------------------------------
+// launch geometry: grids are sized from the device they run on, never from one GPU model's
+// multiprocessor count
+// ---------------------------------------------------------------------------------------------
+
+// multiprocessors of the current device (queried once per device)
+int sm_count();
+// CTAs of `kernel` with `threads` threads and `smem` bytes of dynamic shared memory that are
+// resident on the current device at once (occupancy query x sm_count(), cached per kernel and
+// device); at least sm_count()
+int resident_ctas(const void *kernel, int threads, size_t smem);
+// grid of a grid-stride kernel over `work` items: one CTA per `threads` items, at most `waves`
+// CTAs per multiprocessor
+int grid_for(int64_t work, int threads, int waves = 16);
+
 // validation shared by the entry points
 int check_graph_arg(lagr_graph G, char *msg);
 
@@ -192,7 +207,7 @@ struct TcParams {
 TcParams tc_default_params();
 int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg);
 int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *voff, int32_t ngraphs,
-              unsigned long long *counts, bool orient, cudaStream_t s, char *msg);
+              unsigned long long *counts, bool orient, cudaStream_t s, char *msg, bool count = true);
 unsigned long long *tc_total_slot(Priv *P);
 
 // ---------------------------------------------------------------------------------------------

@@ -1,7 +1,7 @@
-// PageRank (Alg. 3, Sec. IV-C) and its adjoint.
+// PageRank (Alg. 4, Sec. IV-C) and its adjoint.
 //
 // One iteration is one gather over the rows of A' (a "pull" SpMV over the CSC) that fuses every
-// other step of Alg. 3: the teleport assignment, the accumulation r += A' plus.second w, the next
+// other step of Alg. 4: the teleport assignment, the accumulation r += A' plus.second w, the next
 // w = damping * r / d_out (eWiseMult), and per-CTA partial sums of |t - r| (the apply(abs) +
 // reduce of the stopping test) and of the dangling mass.
 //
@@ -35,9 +35,15 @@ constexpr int PR_WUNITS = 1024;   // units per block of the gathers' row plans (
 constexpr int PR_WHEAVY = 1024;   // longer rows are cut into chunks of PR_WHCHUNK entries
 constexpr int PR_WHCHUNK = 2048;
 constexpr int PR_CHUNK = 8;                         // iterations launched between host checks
-constexpr int PR_INIT_BLOCKS = 152 * 8;
 
 constexpr int PR_FIN_BLOCKS = 32;  // CTAs of the partial-sum fold
+
+// the per-CTA partial sums of an iteration: residual, auxiliary sum (dangling mass or v . lambda),
+// L1 norm of the new iterate (adjoint only)
+struct __align__(16) PrSums {
+  double x, y, z, w;
+};
+__host__ __device__ __forceinline__ PrSums pr_sums(double x, double y, double z, double w) { return PrSums{x, y, z, w}; }
 
 struct PrState {
   // read by the host (the first PR_STATE_HOST bytes)
@@ -47,8 +53,9 @@ struct PrState {
   int done;       // set once the tolerance is met or itermax reached
   int iters;      // iterations done
   int queue;      // next row block of the running gather (reset by pr_finalize)
-  // device only: the fold's per-CTA sums and its arrival counter
-  double2 fold[PR_FIN_BLOCKS];
+  // device only: the fold's per-CTA sums (residual, auxiliary sum, L1 norm of the iterate) and its
+  // arrival counter
+  PrSums fold[PR_FIN_BLOCKS];
   unsigned int arrive;
 };
 constexpr size_t PR_STATE_HOST = 32;  // resid, aux, coef, done, iters, queue
@@ -68,7 +75,7 @@ __global__ void pr_scale(const int32_t *__restrict__ rowptr, int32_t n, float da
 template <int MODE>
 __global__ void pr_init(int32_t n, float *__restrict__ x, float *__restrict__ w, const float *__restrict__ sc,
                         const float *__restrict__ src, const float *__restrict__ vvec, float vuni,
-                        double2 *__restrict__ partials) {
+                        PrSums *__restrict__ partials) {
   __shared__ double red[32];
   double aux = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -79,7 +86,7 @@ __global__ void pr_init(int32_t n, float *__restrict__ x, float *__restrict__ w,
     else aux += (sc[i] == 0.0f) ? (double)xi : 0.0;
   }
   aux = block_sum(aux, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(0.0, aux);
+  if (threadIdx.x == 0) partials[blockIdx.x] = pr_sums(0.0, aux, 0.0, 0.0);
 }
 
 struct IterArgs {
@@ -112,7 +119,7 @@ __device__ __forceinline__ float gather_one(const IterArgs &a, int32_t k) {
 // of its float32 rate)
 template <int MODE>
 __device__ __forceinline__ void row_out(const IterArgs &a, int32_t i, float acc, float coef, float &resid,
-                                        float &aux) {
+                                        float &aux, float &nrm) {
   const float vi = a.vvec ? a.vvec[i] : a.vuni;
   const float s = a.sc[i];
   float r;
@@ -127,6 +134,7 @@ __device__ __forceinline__ void row_out(const IterArgs &a, int32_t i, float acc,
   }
   a.out[i] = r;
   resid += fabsf(a.prev[i] - r);
+  if (MODE == 2) nrm += fabsf(r);
   if (MODE == 2) aux += vi * r;
   else if (s == 0.0f) aux += r;
 }
@@ -357,44 +365,49 @@ __global__ void __launch_bounds__(PR_HF_THREADS)
 
 // The element-wise rest of the iteration over the row sums: each row's output (the teleport or
 // adjoint term, the next gathered value, the residual and the dangling / v.lambda sum).  A fixed
-// grid of PR_EPI_BLOCKS CTAs, each with a fixed share of the rows, writes one partial pair per CTA
+// grid of epi_blocks() CTAs, each with a fixed share of the rows, writes one partial pair per CTA
 // (deterministic).
-constexpr int PR_EPI_BLOCKS = 152 * 4;
 template <int MODE>
 __global__ void __launch_bounds__(PR_THREADS)
-    pr_epilogue(IterArgs a, int32_t n, const PrState *__restrict__ st, double2 *__restrict__ partials) {
+    pr_epilogue(IterArgs a, int32_t n, const PrState *__restrict__ st, PrSums *__restrict__ partials) {
   __shared__ double red[32];
   if (st->done) return;
   const float coef = st->coef;
-  float fr = 0.0f, fa = 0.0f;
+  float fr = 0.0f, fa = 0.0f, fn = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    row_out<MODE>(a, (int32_t)i, a.acc[i], coef, fr, fa);
+    row_out<MODE>(a, (int32_t)i, a.acc[i], coef, fr, fa, fn);
   const double resid = block_sum((double)fr, red);
   const double aux = block_sum((double)fa, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(resid, aux);
+  const double nrm = MODE == 2 ? block_sum((double)fn, red) : 0.0;
+  if (threadIdx.x == 0) partials[blockIdx.x] = pr_sums(resid, aux, nrm, 0.0);
 }
 
 // Fold the partials in a fixed order: CTA b sums the b-th contiguous share (a fixed tree), and the
 // CTA that arrives last adds the PR_FIN_BLOCKS sums in order and updates the state (the result does
-// not depend on which CTA is last).  init != 0 only prepares the first coefficient.
+// not depend on which CTA is last).  init != 0 only prepares the first coefficient.  The forward
+// stops when the L1 change is below tol (Alg. 4); the adjoint (mode 2) when it is below tol times
+// the L1 norm of the new iterate (its scale is that of dL/dr, so an absolute bound would be below
+// float32 resolution on large graphs).
 constexpr int PR_FIN_THREADS = 512;
 __global__ void __launch_bounds__(PR_FIN_THREADS)
-    pr_finalize(const double2 *__restrict__ partials, int np, PrState *__restrict__ st, int mode, float damping,
+    pr_finalize(const PrSums *__restrict__ partials, int np, PrState *__restrict__ st, int mode, float damping,
                 int dangling, double tol, int itermax, int init) {
   __shared__ double red[32];
   __shared__ bool last;
   if (!init && st->done) return;  // uniform: done changes only at the end of a fold
   const int per = (np + PR_FIN_BLOCKS - 1) / PR_FIN_BLOCKS;
   const int lo = blockIdx.x * per, hi = min(np, lo + per);
-  double r = 0.0, a = 0.0;
+  double r = 0.0, a = 0.0, nr = 0.0;
   for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     r += partials[i].x;
     a += partials[i].y;
+    nr += partials[i].z;
   }
   r = block_sum(r, red);
   a = block_sum(a, red);
+  nr = block_sum(nr, red);
   if (threadIdx.x == 0) {
-    st->fold[blockIdx.x] = make_double2(r, a);
+    st->fold[blockIdx.x] = pr_sums(r, a, nr, 0.0);
     __threadfence();
     last = atomicAdd(&st->arrive, 1u) == PR_FIN_BLOCKS - 1;
   }
@@ -403,11 +416,14 @@ __global__ void __launch_bounds__(PR_FIN_THREADS)
   __threadfence();
   r = 0.0;
   a = 0.0;
+  nr = 0.0;
   for (int b = 0; b < PR_FIN_BLOCKS; b++) {
     const volatile double *f = reinterpret_cast<volatile double *>(&st->fold[b]);
     r += f[0];
     a += f[1];
+    nr += f[2];
   }
+  if (mode == 2) r = nr > 0.0 ? r / nr : r;  // the adjoint's change relative to its L1 norm
   float coef;
   if (mode == 2) coef = dangling ? (float)((double)damping * a) : 0.0f;
   else coef = (float)((1.0 - (double)damping) + (dangling ? (double)damping * a : 0.0));
@@ -453,40 +469,30 @@ __global__ void pr_teleport_grad(int32_t n, const float *__restrict__ lam, const
     dv[i] = (float)(f * (double)lam[i]);
 }
 
-inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
-  int64_t b = (work + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
-
 }  // namespace
 
 static inline int heavy_finish_blocks(const RowPlan &pl) {
   return (pl.nheavy + PR_HF_THREADS - 1) / PR_HF_THREADS;
 }
 
-static inline int n_partials() { return PR_EPI_BLOCKS > PR_INIT_BLOCKS ? PR_EPI_BLOCKS : PR_INIT_BLOCKS; }
+// fixed grids of the element-wise kernels (the fold's order depends only on the grid): four and
+// eight CTAs per multiprocessor
+static inline int epi_blocks() { return 4 * sm_count(); }
+static inline int init_blocks() { return 8 * sm_count(); }
+static inline int n_partials() { return epi_blocks() > init_blocks() ? epi_blocks() : init_blocks(); }
 
 static inline int aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // one iteration: the row-sum gather, the heavy rows' chunk sums, the element-wise epilogue and the
 // fold of its partials
 template <int MODE>
-static void launch_iter(const RowPlan &pl, const IterArgs &a, int32_t n, PrState *st, double2 *partials,
+static void launch_iter(const RowPlan &pl, const IterArgs &a, int32_t n, PrState *st, PrSums *partials,
                         int32_t itermax, double tol, cudaStream_t s) {
   // as many persistent CTAs as can be resident at once (no more than there are warp items)
-  static int resident[3] = {0, 0, 0};
-  if (resident[MODE] == 0) {
-    int per_sm = 0, dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr_warp<MODE>, PR_THREADS, 0);
-    resident[MODE] = (per_sm > 0 && nsm > 0) ? per_sm * nsm : 152;
-  }
+  const int resident = resident_ctas((const void *)pr_warp<MODE>, PR_THREADS, 0);
   const int64_t items = (int64_t)pl.nhc + pl.nblk;
   const int64_t need = (items * 32 + PR_THREADS - 1) / PR_THREADS;
-  const int grid = (int)(need < resident[MODE] ? (need > 0 ? need : 1) : resident[MODE]);
+  const int grid = (int)(need < resident ? (need > 0 ? need : 1) : resident);
   {
     KTimer kt(TK_PR_GATHER, s);
     pr_warp<MODE><<<grid, PR_THREADS, 0, s>>>(a, pl.blk, pl.nblk, pl.hblk, pl.heavy, pl.hc_off, pl.hc_row, pl.nhc,
@@ -494,22 +500,24 @@ static void launch_iter(const RowPlan &pl, const IterArgs &a, int32_t n, PrState
   }
   const int hfb = heavy_finish_blocks(pl);
   if (hfb > 0) pr_heavy_finish<<<hfb, PR_HF_THREADS, 0, s>>>(a, pl.heavy, pl.nheavy, pl.hc_off, st);
-  pr_epilogue<MODE><<<PR_EPI_BLOCKS, PR_THREADS, 0, s>>>(a, n, st, partials);
-  pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials, PR_EPI_BLOCKS, st, MODE, a.damping, a.dangling, tol,
+  const int eb = epi_blocks();
+  pr_epilogue<MODE><<<eb, PR_THREADS, 0, s>>>(a, n, st, partials);
+  pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials, eb, st, MODE, a.damping, a.dangling, tol,
                                                        itermax, 0);
 }
 
-// start vector, w0 and the first coefficient (the init partials use the first PR_INIT_BLOCKS slots)
+// start vector, w0 and the first coefficient (the init partials use the first init_blocks() slots)
 static void launch_init(int mode, int32_t n, float *x, float *w, const float *sc, const float *src, const float *vvec,
-                        float vuni, PrState *st, double2 *partials, float damping, int dangling, int32_t itermax,
+                        float vuni, PrState *st, PrSums *partials, float damping, int dangling, int32_t itermax,
                         double tol, cudaStream_t s) {
+  const int ib = init_blocks();
   if (mode == 2)
-    pr_init<2><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
+    pr_init<2><<<ib, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
   else if (mode == 1)
-    pr_init<1><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
+    pr_init<1><<<ib, PR_THREADS, 0, s>>>(n, x, nullptr, sc, src, vvec, vuni, partials);
   else
-    pr_init<0><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(n, x, w, sc, src, vvec, vuni, partials);
-  pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials, PR_INIT_BLOCKS, st, mode, damping, dangling, tol,
+    pr_init<0><<<ib, PR_THREADS, 0, s>>>(n, x, w, sc, src, vvec, vuni, partials);
+  pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials, ib, st, mode, damping, dangling, tol,
                                                        itermax, 1);
 }
 
@@ -523,7 +531,7 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const in
   const int32_t n = G->n;
   const int vec = aligned16(colidx) && (val == nullptr || aligned16(val));
   Temp<float> buf1(s), w0(s), w1(s), hpart(s), rsum(s);
-  Temp<double2> partials(s);
+  Temp<PrSums> partials(s);
   LAGR_TRY(buf1.alloc(n, msg, "PageRank work vector"));
   LAGR_TRY(rsum.alloc(n, msg, "PageRank row sums"));
   LAGR_TRY(hpart.alloc((size_t)pl.nhc + 1, msg, "heavy chunk sums"));
@@ -533,7 +541,7 @@ static int pr_solve(int mode, lagr_graph G, Priv *P, const RowPlan &pl, const in
   }
   const int np = n_partials();
   LAGR_TRY(partials.alloc(np, msg, "PageRank partial sums"));
-  LAGR_CUDA_TRY(cudaMemsetAsync(partials.p, 0, np * sizeof(double2), s));
+  LAGR_CUDA_TRY(cudaMemsetAsync(partials.p, 0, np * sizeof(PrSums), s));
   LAGR_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(PrState), s));
   const float vuni = 1.0f / (float)n;
   float *x[2] = {buf0, buf1.p};
@@ -604,7 +612,7 @@ struct PrPlan {
   const float *vvec = nullptr;
   float damping = 0.85f;
   float *sc = nullptr, *x1 = nullptr, *w0 = nullptr, *w1 = nullptr, *hpart = nullptr, *rsum = nullptr;
-  double2 *partials = nullptr;
+  PrSums *partials = nullptr;
   int np = 0;
   PrState *st = nullptr;
 };
@@ -644,7 +652,7 @@ int pr_plan_enqueue(PrPlan *pl, float *out, const float *warm, int32_t iters, cu
   const float vuni = 1.0f / (float)pl->n;
   float *x[2] = {out, pl->x1};
   float *w[2] = {pl->w0, pl->w1};
-  LAGR_CUDA_TRY(cudaMemsetAsync(pl->partials, 0, pl->np * sizeof(double2), s));
+  LAGR_CUDA_TRY(cudaMemsetAsync(pl->partials, 0, pl->np * sizeof(PrSums), s));
   LAGR_CUDA_TRY(cudaMemsetAsync(pl->st, 0, sizeof(PrState), s));
   launch_init(0, pl->n, out, w[0], pl->sc, warm, pl->vvec, vuni, pl->st, pl->partials, pl->damping, 0, iters, 0.0, s);
   for (int k = 1; k <= iters; k++) {
@@ -773,13 +781,14 @@ extern "C" int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t
   }
   if (dL_dteleport) {
     // delta = dangling mass of r, through the init reduction (aux slot)
-    Temp<double2> partials(s);
+    Temp<PrSums> partials(s);
     Temp<float> scratch(s);
-    LAGR_TRY(partials.alloc(PR_INIT_BLOCKS, msg, "partials"));
+    const int ib = init_blocks();
+    LAGR_TRY(partials.alloc(ib, msg, "partials"));
     LAGR_TRY(scratch.alloc(G->n, msg, "scratch"));
-    pr_init<1><<<PR_INIT_BLOCKS, PR_THREADS, 0, s>>>(G->n, scratch.p, nullptr, sc.p, r, teleport, 1.0f / (float)G->n,
+    pr_init<1><<<ib, PR_THREADS, 0, s>>>(G->n, scratch.p, nullptr, sc.p, r, teleport, 1.0f / (float)G->n,
                                                    partials.p);
-    pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials.p, PR_INIT_BLOCKS, st.p, 1, damping, dangling, 0.0,
+    pr_finalize<<<PR_FIN_BLOCKS, PR_FIN_THREADS, 0, s>>>(partials.p, ib, st.p, 1, damping, dangling, 0.0,
                                                          1, 1);
     pr_teleport_grad<<<grid_for(G->n, 256), 256, 0, s>>>(G->n, lam.p, st.p, damping, dangling, dL_dteleport);
     LAGR_LAUNCH_CHECK();
@@ -789,7 +798,7 @@ extern "C" int lagr_pagerank_backward(float *dL_dw, float *dL_dteleport, int32_t
   G->last_iters = k;
   G->last_resid = resid;
   if (tol > 0.0f && !(resid < (double)tol)) {
-    set_msg(msg, "adjoint stopped at itermax=%d with L1 change %g >= tol %g", itermax, resid, (double)tol);
+    set_msg(msg, "adjoint stopped at itermax=%d with relative L1 change %g >= tol %g", itermax, resid, (double)tol);
     return LAGR_WARN_NOT_CONVERGED;
   }
   clear_msg(msg);

@@ -271,13 +271,6 @@ __global__ void heavy_chunk_rows(const int32_t *__restrict__ hc_off, int32_t nh,
     for (int32_t c = hc_off[h]; c < hc_off[h + 1]; c++) hc_row[c] = (int32_t)h;
 }
 
-inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
-  int64_t b = (work + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
-
 }  // namespace
 
 int64_t scan_scratch_len(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }

@@ -1,4 +1,4 @@
-// Triangle counting (Alg. 6, Sec. IV-F): t = sum(C) with C<s(L)> = L plus.pair U', fused so
+// Triangle counting (Alg. 6, Sec. IV-E): t = sum(C) with C<s(L)> = L plus.pair U', fused so
 // that C is never formed (the materialised C is what the paper blames for its 3x gap to GAP).
 //
 // Labels.  Alg. 6 relabels A by the ascending-degree permutation p (A(p,p)) before splitting it
@@ -17,6 +17,7 @@
 // probe is one shared-memory word, and an entry ranked below the anchor is rejected without any
 // lookup (it cannot be in the anchor's list).  Anchors with short lists run one per warp; long
 // lists or many neighbours run one CTA per (anchor, chunk of neighbours).
+#include <atomic>
 #include <cstring>
 
 #include "internal.cuh"
@@ -418,15 +419,7 @@ __global__ void __launch_bounds__(TCS_WARPS * 32)
 // one wave of a warp sorter instance: every warp resident at once
 template <int PMAX>
 int sort_wave_ctas() {
-  static int ctas = 0;
-  if (ctas == 0) {
-    int per_sm = 0, dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_sort_rows_warp<PMAX>, TCS_WARPS * 32, 0);
-    ctas = (per_sm > 0 && nsm > 0) ? per_sm * nsm : 152 * 4;
-  }
-  return ctas;
+  return resident_ctas((const void *)tc_sort_rows_warp<PMAX>, TCS_WARPS * 32, 0);
 }
 
 // the rows of TC_SORT_WARP < d+ <= TC_SORT_MAX: one CTA each (dynamic shared memory TC_SORT_MAX ints)
@@ -751,16 +744,176 @@ __global__ void __launch_bounds__(TCC_THREADS)
   }
 }
 
-inline int grid_for(int64_t work, int threads, int cap = 152 * 16) {
-  int64_t b = (work + threads - 1) / threads;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
+// ---- C<s(L)> kept (the unfused form of Alg. 6) --------------------------------------------------
+//
+// C(i,j) at an entry of L (rank i > rank j) counts the k with j < k < i adjacent to both, i.e. the
+// k in U(j) whose own list U(k) holds i.  So the lowest vertex j of each triangle is the anchor:
+// its list U(j) goes into a hash table keyed by rank with a counter per key, every list U(k) of a
+// k in U(j) is probed against it, and a hit on key i counts one triangle (j, k, i) for C(i, j).
+// The counts are then written to the stored entry (i, j) of A (row i, found by binary search).
+// Every anchor owns its table, so the counts are exact; their sum is t.  Anchors with d+ <= 256
+// run one per warp (a 512-slot table in shared memory), those up to KEPT_CTA_MAXD one per CTA
+// (the table in shared memory), longer ones one per CTA with the table in global memory.
+
+constexpr int KEPT_WSLOTS = 512;
+constexpr int KEPT_WMAXD = KEPT_WSLOTS / 2;
+constexpr int KEPT_CTA_MAXD = 8192;
+constexpr int KEPT_THREADS = 256;
+constexpr int KEPT_SLOTS_MAX = 2 * KEPT_CTA_MAXD;  // table slots of the largest shared-memory table
+enum KeptSlot { KS_NW = 0, KS_NC = 1, KS_NH = 2, KS_QW = 3, KS_QC = 4, KS_QH = 5, KS_TOTAL = 6, KS_HSLOTS = 7,
+                KS_NSLOT = 8 };
+
+__device__ __forceinline__ int hfind(const int32_t *tab, int logT, int32_t w) {
+  const uint32_t mask = (1u << logT) - 1;
+  uint32_t h = hslot(w, logT);
+  for (uint32_t i = 0; i <= mask; i++) {
+    const int32_t v = tab[h];
+    if (v == w) return (int)h;
+    if (v == EMPTY) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// rank -> vertex id
+__global__ void tc_rank_inverse(const int32_t *__restrict__ rank, int32_t n, int32_t *__restrict__ inv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    inv[rank[i]] = (int32_t)i;
+}
+
+// the anchors by class; the global tables of the longest ones get their slot counts in hsz
+__global__ void tc_kept_classify(const int32_t *__restrict__ dplus, int32_t n, int32_t *__restrict__ lw,
+                                 int32_t *__restrict__ lc, int32_t *__restrict__ lh, int32_t *__restrict__ hsz,
+                                 int64_t *__restrict__ ks) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = dplus[v];
+    if (a <= 0) continue;
+    if (a <= KEPT_WMAXD) {
+      lw[atomicAdd((unsigned long long *)&ks[KS_NW], 1ull)] = (int32_t)v;
+    } else if (a <= KEPT_CTA_MAXD) {
+      lc[atomicAdd((unsigned long long *)&ks[KS_NC], 1ull)] = (int32_t)v;
+    } else {
+      const unsigned long long p = atomicAdd((unsigned long long *)&ks[KS_NH], 1ull);
+      lh[p] = (int32_t)v;
+      hsz[p] = 1 << ceil_log2(2 * a);
+    }
+  }
+}
+
+// One anchor v, processed by `ng` warps of a group (warp index gw within it) with the table
+// (keys, cnt) of 2^logT slots; sync() is the group's barrier.  Writes the anchor's C values into c
+// and adds their sum into *total.
+template <class Sync>
+__device__ __forceinline__ void kept_anchor(int32_t v, const int32_t *__restrict__ rowptr,
+                                            const int32_t *__restrict__ colidx, const int32_t *__restrict__ dplus,
+                                            const int32_t *__restrict__ u_colidx, const int32_t *__restrict__ inv,
+                                            int32_t *keys, uint32_t *cnt, int logT, int gw, int ng, int gtid,
+                                            int gsize, Sync &&sync, uint32_t *__restrict__ c,
+                                            unsigned long long *__restrict__ total) {
+  const int lane = threadIdx.x & 31;
+  const int32_t a = dplus[v];
+  const int32_t ub = rowptr[v];
+  const int T = 1 << logT;
+  for (int i = gtid; i < T; i += gsize) {
+    keys[i] = EMPTY;
+    cnt[i] = 0u;
+  }
+  sync();
+  for (int i = gtid; i < a; i += gsize) hinsert(keys, logT, u_colidx[ub + i]);
+  sync();
+  // the middle vertices k in U(v), 32 per warp batch: probe every entry of U(k) against U(v)
+  for (int32_t jb = gw * 32; jb < a; jb += ng * 32) {
+    const int32_t j = jb + lane;
+    int32_t st = 0, len = 0;
+    if (j < a) {
+      const int32_t k = inv[u_colidx[ub + j]];
+      st = rowptr[k];
+      len = dplus[k];
+    }
+    warp_segments(st, len, 0, [&](bool valid, int, int, int gidx) {
+      if (valid) {
+        const int slot = hfind(keys, logT, u_colidx[gidx]);
+        if (slot >= 0) atomicAdd(&cnt[slot], 1u);
+      }
+    });
+  }
+  sync();
+  // C(i, v) for every i in U(v), into the entry (i, v) of A
+  unsigned long long mine = 0;
+  for (int q = gtid; q < T; q += gsize) {
+    const int32_t r = keys[q];
+    if (r == EMPTY) continue;
+    const uint32_t cv = cnt[q];
+    if (cv == 0) continue;  // c is cleared before the pass
+    const int32_t top = inv[r];
+    int32_t lo = rowptr[top], hi = rowptr[top + 1];
+    while (lo < hi) {
+      const int32_t mid = lo + ((hi - lo) >> 1);
+      if (colidx[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    if (lo < rowptr[top + 1] && colidx[lo] == v) {  // present on a symmetric graph
+      c[lo] = cv;
+      mine += cv;
+    }
+  }
+  mine = warp_sum(mine);
+  if (lane == 0 && mine) atomicAdd(total, mine);
+  sync();
+}
+
+// warp-class anchors: one per warp, table in shared memory
+__global__ void __launch_bounds__(KEPT_THREADS)
+    tc_kept_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                 const int32_t *__restrict__ dplus, const int32_t *__restrict__ u_colidx,
+                 const int32_t *__restrict__ inv, const int32_t *__restrict__ list, int64_t *__restrict__ ks,
+                 uint32_t *__restrict__ c) {
+  __shared__ int32_t skeys[KEPT_THREADS / 32][KEPT_WSLOTS];
+  __shared__ uint32_t scnt[KEPT_THREADS / 32][KEPT_WSLOTS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nl = ks[KS_NW];
+  for (;;) {
+    long long it = 0;
+    if (lane == 0) it = (long long)atomicAdd((unsigned long long *)&ks[KS_QW], 1ull);
+    it = __shfl_sync(LAGR_FULL_MASK, it, 0);
+    if (it >= nl) break;
+    const int32_t v = list[it];
+    kept_anchor(v, rowptr, colidx, dplus, u_colidx, inv, skeys[warp], scnt[warp], ceil_log2(2 * dplus[v]), 0, 1,
+                lane, 32, [] { __syncwarp(); }, c, (unsigned long long *)&ks[KS_TOTAL]);
+  }
+}
+
+// CTA-class anchors (table in dynamic shared memory) or, with gkeys != NULL, the longest anchors
+// (table at gkeys + hoff[i] in global memory)
+__global__ void __launch_bounds__(KEPT_THREADS)
+    tc_kept_cta(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                const int32_t *__restrict__ dplus, const int32_t *__restrict__ u_colidx,
+                const int32_t *__restrict__ inv, const int32_t *__restrict__ list, int64_t *__restrict__ ks,
+                int slot_n, int slot_q, int32_t *__restrict__ gkeys, uint32_t *__restrict__ gcnt,
+                const int32_t *__restrict__ hoff, uint32_t *__restrict__ c) {
+  extern __shared__ int32_t ksm[];
+  __shared__ long long s_it;
+  const int64_t nl = ks[slot_n];
+  for (;;) {
+    if (threadIdx.x == 0) s_it = (long long)atomicAdd((unsigned long long *)&ks[slot_q], 1ull);
+    __syncthreads();
+    const long long it = s_it;
+    __syncthreads();
+    if (it >= nl) break;
+    const int32_t v = list[it];
+    const int logT = ceil_log2(2 * dplus[v]);
+    int32_t *keys = gkeys ? gkeys + hoff[it] : ksm;
+    uint32_t *cnt = gkeys ? gcnt + hoff[it] : reinterpret_cast<uint32_t *>(ksm + KEPT_SLOTS_MAX);
+    kept_anchor(v, rowptr, colidx, dplus, u_colidx, inv, keys, cnt, logT, threadIdx.x >> 5, blockDim.x >> 5,
+                threadIdx.x, blockDim.x, [] { __syncthreads(); }, c, (unsigned long long *)&ks[KS_TOTAL]);
+  }
 }
 
 }  // namespace
 
 TcParams tc_default_params() { return TcParams{TCC_CHUNK, TCW_MAXD}; }
+
+// capacities of the anchor lists forced by lagr_debug_tc_capacity (0: computed from the graph)
+static std::atomic<int64_t> g_force_capc{0}, g_force_capwh{0};
 
 // Allocate the orientation U (on G) and the anchor lists / orientation scratch (in the private
 // state) for the given work partition.  No kernels.
@@ -771,8 +924,18 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
     set_msg(msg, "bad triangle-count partition (wmax=%d, chunk=%d)", prm.wmax, prm.chunk);
     return LAGR_ERR_INVALID_VALUE;
   }
-  const int64_t capc = 2 * (nnz / (prm.wmax + 1) + nnz / (TCW_MAXDEG + 1)) + nnz / prm.chunk + 64;
-  if (G->u_colidx && P->tc_listw && P->tc_capc >= capc) return LAGR_OK;
+  // Capacity of the CTA item list: anchors outside the warp class have d+ > wmax (at most
+  // m_L / (wmax + 1) = nnz / (2 (wmax + 1)) of them, as the d+ sum to m_L) or degree > TCW_MAXDEG
+  // (at most nnz / (TCW_MAXDEG + 1)), and each has ceil(deg / chunk) <= deg / chunk + 1 items: at
+  // most nnz / chunk + nnz / (2 (wmax + 1)) + nnz / (TCW_MAXDEG + 1) items in all on a symmetric
+  // graph.  Writes past the capacity are skipped and flag SC_ERR; the count kernels read at most
+  // the capacity (see tc_classify, tc_count_cta, tc_count_warp).
+  const int64_t fc = g_force_capc.load(), fwh = g_force_capwh.load();
+  const int64_t capc = fc > 0 ? fc : 2 * (nnz / (prm.wmax + 1) + nnz / (TCW_MAXDEG + 1)) + nnz / prm.chunk + 64;
+  const int64_t capwh = fwh > 0 ? fwh : 2 * (nnz / TCW_CHUNK) + 64;
+  if (G->u_colidx && P->tc_listw && P->tc_capc >= capc && P->tc_capwh >= capwh &&
+      (fc == 0 || P->tc_capc == capc) && (fwh == 0 || P->tc_capwh == capwh))
+    return LAGR_OK;
   dev_free(G->u_dplus, s);
   dev_free(G->u_colidx, s);
   G->u_dplus = G->u_colidx = nullptr;
@@ -796,8 +959,8 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
   LAGR_TRY(alloc_n(&G->u_dplus, (size_t)n + 1, s, msg, "d+"));
   LAGR_TRY(alloc_n(&G->u_colidx, (size_t)(nnz > 0 ? nnz : 1), s, msg, "U column indices"));
   LAGR_TRY(alloc_n(&P->tc_listw, (size_t)n + 1, s, msg, "warp anchors"));
-  // warp anchors cut into items: ceil(deg / TCW_CHUNK) <= 2 deg / TCW_CHUNK items each (deg > TCW_CHUNK)
-  const int64_t capwh = 2 * (nnz / TCW_CHUNK) + 64;
+  // warp anchors cut into items: ceil(deg / TCW_CHUNK) <= 2 deg / TCW_CHUNK items each (deg > TCW_CHUNK),
+  // capacity capwh above
   LAGR_TRY(alloc_n(&P->tc_listwh, (size_t)capwh, s, msg, "warp anchor items"));
   P->tc_capwh = capwh;
   LAGR_TRY(alloc_n(&P->tc_listc, (size_t)capc, s, msg, "CTA anchors"));
@@ -813,7 +976,7 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
 // memsets only (capturable in a CUDA graph).  counts[] receives the total (or per-member totals
 // when voff != NULL; counts is zeroed here).  The Alg. 6 sort decision is taken on the device.
 int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *voff, int32_t ngraphs,
-              unsigned long long *counts, bool orient, cudaStream_t s, char *msg) {
+              unsigned long long *counts, bool orient, cudaStream_t s, char *msg, bool count) {
   const int32_t n = G->n;
   const int64_t nnz = G->nnz;
   LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_sort_rows_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -838,7 +1001,7 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
     const RowPlan &rp = P->pr_at;
     tc_orient_rows<<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, G->u_dplus, G->u_colidx);
     if (rp.nheavy > 0)
-      tc_orient_heavy<<<152 * 2, 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, G->u_dplus, G->u_colidx, rp.heavy,
+      tc_orient_heavy<<<2 * sm_count(), 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, G->u_dplus, G->u_colidx, rp.heavy,
                                               rp.nheavy);
     {  // the rows to sort are listed in the rank-sort buffers (4n ints, free again once the ranks
        // are made): n pairs for the short rows, then n shared by the CTA rows and the long ones
@@ -848,7 +1011,7 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
           lw, 0, P->dscal, SL_NSW, G->u_colidx);
       tc_sort_rows_warp<TC_SORT_WARP><<<sort_wave_ctas<TC_SORT_WARP>(), TCS_WARPS * 32, 0, s>>>(
           lm_end, 1, P->dscal, SL_NSM, G->u_colidx);
-      tc_sort_rows_cta<<<152, TCS_CTA_THREADS, TC_SORT_MAX * sizeof(int32_t), s>>>(lc, P->dscal, G->u_colidx);
+      tc_sort_rows_cta<<<sm_count(), TCS_CTA_THREADS, TC_SORT_MAX * sizeof(int32_t), s>>>(lc, P->dscal, G->u_colidx);
     }
     tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, P->tc_listw, P->tc_listwh,
                                                  P->tc_capwh, P->tc_listc, P->tc_capc, P->dscal, prm.wmax,
@@ -859,6 +1022,7 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
     LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal + SL_QW, 0, 3 * sizeof(int64_t), s));
     LAGR_CUDA_TRY(cudaMemsetAsync(P->dscal + SL_QWL, 0, sizeof(int64_t), s));
   }
+  if (!count) return LAGR_OK;  // the orientation alone (the kept-C form counts on its own)
   if (counts != (unsigned long long *)(P->dscal + SL_TOTAL))
     LAGR_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ngraphs * sizeof(unsigned long long), s));
   // windows: the top ranks [n - window, n) (or all of them on small graphs)
@@ -866,13 +1030,13 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
   const int32_t w0w = n > (1 << TCW_WIN_LOG) ? n - (1 << TCW_WIN_LOG) : 0;
   {
     KTimer kt(TK_TC_CTA, s);
-    tc_count_cta<<<152 * 4, TCC_THREADS, TCC_SMEM, s>>>(G->rowptr, G->colidx, G->rowptr, G->u_colidx, G->u_dplus,
+    tc_count_cta<<<resident_ctas((const void *)tc_count_cta, TCC_THREADS, TCC_SMEM), TCC_THREADS, TCC_SMEM, s>>>(G->rowptr, G->colidx, G->rowptr, G->u_colidx, G->u_dplus,
                                                         P->tc_rank, P->tc_listc, P->dscal, w0c, voff, ngraphs, counts,
                                                         prm.chunk, P->tc_capc);
   }
   {
     KTimer kt(TK_TC_WARP, s);
-    tc_count_warp<<<152 * 4, TCW_WARPS * 32, TCW_SMEM, s>>>(G->rowptr, G->colidx, G->rowptr, G->u_colidx,
+    tc_count_warp<<<resident_ctas((const void *)tc_count_warp, TCW_WARPS * 32, TCW_SMEM), TCW_WARPS * 32, TCW_SMEM, s>>>(G->rowptr, G->colidx, G->rowptr, G->u_colidx,
                                                             G->u_dplus, P->tc_rank, P->tc_listw, n, P->tc_listwh,
                                                             P->tc_capwh, P->dscal, w0w,
                                                             voff, ngraphs, counts);
@@ -910,16 +1074,102 @@ extern "C" int lagr_tc(uint64_t *ntriangles, lagr_graph G, int32_t method, void 
   Priv *P = nullptr;
   LAGR_TRY(priv_get(G, s, msg, &P));
   const TcParams prm = tc_default_params();
+  LAGR_TRY(tc_alloc(G, P, prm, s, msg));  // (re)allocating resets u_order: the orientation is rebuilt
   const bool cached = G->u_colidx && G->u_order == method && P->tc_listw;
-  LAGR_TRY(tc_alloc(G, P, prm, s, msg));
   LAGR_TRY(tc_launch(G, P, method, prm, nullptr, 1, tc_total_slot(P), !cached, s, msg));
   G->u_order = method;
   LAGR_TRY(fetch_to_host(P->hscal, P->dscal, LAGR_NSCAL * sizeof(int64_t), s, msg));
   if (P->hscal[SC_ERR] != 0) {
-    set_msg(msg, "oriented graph overflowed: the undirected graph is not symmetric");
+    set_msg(msg, "an anchor list overflowed its capacity (an undirected graph that is not symmetric, or "
+                 "capacities forced by lagr_debug_tc_capacity); the count is incomplete");
     return LAGR_ERR_INVALID_GRAPH;
   }
   *ntriangles = (uint64_t)P->hscal[SL_TOTAL];
+  clear_msg(msg);
+  return LAGR_OK;
+}
+
+extern "C" int lagr_debug_tc_capacity(int64_t capc, int64_t capwh) {
+  if (capc < 0 || capwh < 0) return LAGR_ERR_INVALID_VALUE;
+  g_force_capc.store(capc);
+  g_force_capwh.store(capwh);
+  return LAGR_OK;
+}
+
+extern "C" int lagr_tc_edges(uint32_t *c, uint64_t *ntriangles, lagr_graph G, int32_t method, void *stream,
+                             char *msg) {
+  LAGR_TRY(check_graph_arg(G, msg));
+  if (!c && G->nnz > 0) {
+    set_msg(msg, "c is NULL");
+    return LAGR_ERR_NULL_POINTER;
+  }
+  if (method != LAGR_TC_AUTO && method != LAGR_TC_SORT && method != LAGR_TC_NOSORT) {
+    set_msg(msg, "unknown triangle-count method %d", method);
+    return LAGR_ERR_INVALID_VALUE;
+  }
+  if (G->kind != LAGR_UNDIRECTED) {
+    set_msg(msg, "triangle counting needs an undirected graph");
+    return LAGR_ERR_INVALID_GRAPH;
+  }
+  if (ntriangles) *ntriangles = 0;
+  const int32_t n = G->n;
+  const int64_t nnz = G->nnz;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0 || nnz == 0) {
+    clear_msg(msg);
+    return LAGR_OK;
+  }
+  Priv *P = nullptr;
+  LAGR_TRY(priv_get(G, s, msg, &P));
+  const TcParams prm = tc_default_params();
+  LAGR_TRY(tc_alloc(G, P, prm, s, msg));
+  const bool cached = G->u_colidx && G->u_order == method && P->tc_listw;
+  if (!cached) {
+    LAGR_TRY(tc_launch(G, P, method, prm, nullptr, 1, tc_total_slot(P), true, s, msg, false));
+    G->u_order = method;
+  }
+  Temp<int32_t> inv(s), lw(s), lc(s), lh(s), hsz(s), hoff(s);
+  Temp<int64_t> ks(s);
+  LAGR_TRY(inv.alloc(n, msg, "rank inverse"));
+  LAGR_TRY(lw.alloc(n, msg, "warp anchors"));
+  LAGR_TRY(lc.alloc(n, msg, "CTA anchors"));
+  LAGR_TRY(lh.alloc(n, msg, "long anchors"));
+  LAGR_TRY(hsz.alloc(n, msg, "table sizes"));
+  LAGR_TRY(hoff.alloc((size_t)n + 1, msg, "table offsets"));
+  LAGR_TRY(ks.alloc(KS_NSLOT, msg, "counters"));
+  LAGR_CUDA_TRY(cudaMemsetAsync(ks.p, 0, KS_NSLOT * sizeof(int64_t), s));
+  LAGR_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)nnz * sizeof(uint32_t), s));
+  tc_rank_inverse<<<grid_for(n, 256), 256, 0, s>>>(P->tc_rank, n, inv.p);
+  tc_kept_classify<<<grid_for(n, 256), 256, 0, s>>>(G->u_dplus, n, lw.p, lc.p, lh.p, hsz.p, ks.p);
+  LAGR_LAUNCH_CHECK();
+  int64_t h[KS_NSLOT];
+  LAGR_TRY(fetch_to_host(h, ks.p, sizeof(h), s, msg));
+  const int64_t nh = h[KS_NH];
+  Temp<int32_t> gkeys(s);
+  Temp<uint32_t> gcnt(s);
+  if (nh > 0) {  // global tables of the longest anchors: one after the other
+    LAGR_TRY(exclusive_scan(hsz.p, hoff.p, nh, s, msg));
+    int32_t tot = 0;
+    const int32_t *src[1] = {hoff.p + nh};
+    LAGR_TRY(fetch_i32s(&tot, src, 1, s, msg));
+    LAGR_TRY(gkeys.alloc(tot, msg, "anchor tables"));
+    LAGR_TRY(gcnt.alloc(tot, msg, "anchor counters"));
+  }
+  const size_t csmem = (size_t)2 * KEPT_SLOTS_MAX * sizeof(int32_t);
+  LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_kept_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+  if (h[KS_NW] > 0)
+    tc_kept_warp<<<resident_ctas((const void *)tc_kept_warp, KEPT_THREADS, 0), KEPT_THREADS, 0, s>>>(
+        G->rowptr, G->colidx, G->u_dplus, G->u_colidx, inv.p, lw.p, ks.p, c);
+  if (h[KS_NC] > 0)
+    tc_kept_cta<<<resident_ctas((const void *)tc_kept_cta, KEPT_THREADS, csmem), KEPT_THREADS, csmem, s>>>(
+        G->rowptr, G->colidx, G->u_dplus, G->u_colidx, inv.p, lc.p, ks.p, KS_NC, KS_QC, nullptr, nullptr, nullptr,
+        c);
+  if (nh > 0)
+    tc_kept_cta<<<sm_count(), KEPT_THREADS, 0, s>>>(G->rowptr, G->colidx, G->u_dplus, G->u_colidx, inv.p, lh.p,
+                                                    ks.p, KS_NH, KS_QH, gkeys.p, gcnt.p, hoff.p, c);
+  LAGR_LAUNCH_CHECK();
+  LAGR_TRY(fetch_to_host(h, ks.p, sizeof(h), s, msg));
+  if (ntriangles) *ntriangles = (uint64_t)h[KS_TOTAL];
   clear_msg(msg);
   return LAGR_OK;
 }

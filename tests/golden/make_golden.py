@@ -4,7 +4,7 @@ closed_forms.json: values that follow from closed forms alone (no oracle, no
 CUDA path), each with its derivation:
   * triangles of K_n = C(n,3); of the wheel W_k (hub + k-cycle, k >= 4) = k;
     of the 4-neighbour grid = 0 (bipartite).
-  * PageRank (GAP form, Alg. 3) on the star K_{1,s}: with a = (1-alpha)/n,
+  * PageRank (GAP form, Alg. 4) on the star K_{1,s}: with a = (1-alpha)/n,
     n = s+1, the centre gets alpha*r_l from each leaf (leaf degree 1) and each
     leaf gets alpha*r_c/s, so r_c = a + alpha*s*r_l and r_l = a + alpha*r_c/s,
     giving r_c = a(1 + alpha*s)/(1 - alpha^2).
@@ -13,7 +13,13 @@ rmat12_oracle.json: the oracle's results on the seeded R-MAT scale-12 graph
 (edge factor 16, seed 20210404), written by calling only ``gen`` and
 ``oracle``.
 
-Run from the repository root:  python tests/golden/make_golden.py
+rmat22_oracle.json: the oracle's results on the benchmark graph, R-MAT scale
+22 (edge factor 16, seed 20210404): the triangle count of Alg. 6 as written
+(method AUTO; several minutes on one core) and, for each of the 16 seeded BFS
+sources, the depth and level histogram of Alg. 1.  Written by calling only
+``gen`` and ``oracle``.
+
+Run from the repository root:  python tests/golden/make_golden.py [--skip-rmat22]
 """
 import json
 import math
@@ -41,8 +47,8 @@ def closed_forms():
         rl = a + alpha * rc / s
         star.append({"s": s, "alpha": alpha, "r_centre": rc, "r_leaf": rl})
     return {
-        "triangles": {"source": "closed forms (Alg. 6 counts unique 3-cliques, Sec. IV-F)", "cases": tri},
-        "pagerank_star": {"source": "fixed point of Alg. 3 (Sec. IV-C) on K_{1,s}, solved by hand",
+        "triangles": {"source": "closed forms (Alg. 6 counts unique 3-cliques, Sec. IV-E)", "cases": tri},
+        "pagerank_star": {"source": "fixed point of Alg. 4 (Sec. IV-C) on K_{1,s}, solved by hand",
                           "cases": star},
     }
 
@@ -60,8 +66,28 @@ def rmat12():
     }
 
 
+def rmat22():
+    seed = 20210404
+    g = gen.rmat(22, 16, seed=seed)
+    srcs = [int(s) for s in gen.sources(g, 16, seed=seed)]
+    bfs = []
+    for s in srcs:
+        level, _, depth = oracle.bfs(g, s)
+        bfs.append({"source": s, "depth": depth, "level_histogram": np.bincount(level[level >= 0]).tolist()})
+    return {
+        "graph": "R-MAT scale 22, edge factor 16, a/b/c = .57/.19/.19, seed 20210404, symmetrised, deduplicated",
+        "nnz": g.nnz,
+        "triangles": oracle.tc(g, oracle.TC_AUTO),
+        "sources": srcs,
+        "bfs": bfs,
+    }
+
+
 if __name__ == "__main__":
     with open(os.path.join(HERE, "closed_forms.json"), "w") as f:
         json.dump(closed_forms(), f, indent=1)
     with open(os.path.join(HERE, "rmat12_oracle.json"), "w") as f:
         json.dump(rmat12(), f, indent=1)
+    if "--skip-rmat22" not in sys.argv:
+        with open(os.path.join(HERE, "rmat22_oracle.json"), "w") as f:
+            json.dump(rmat22(), f, indent=1)

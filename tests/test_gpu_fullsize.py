@@ -1,11 +1,14 @@
 """Parity at the full benchmark sizes, in the configuration bench.py times.
 
 Where the single-threaded oracle finishes in seconds (BFS, a fixed number of PageRank iterations,
-the adjoint) the GPU result is compared element by element; where it cannot (the triangle count of
-the scale-22 R-MAT) properties that hold at any size are checked instead: the count is invariant
-under relabelling and under the choice of orientation, and every member of a batch equals its own
-plain call.
+the adjoint) the GPU result is compared element by element; the triangle count of the scale-22
+R-MAT (minutes of oracle time) is compared with the oracle's count stored in
+tests/golden/rmat22_oracle.json by tests/golden/make_golden.py, and is also checked for invariance
+under relabelling and under the choice of orientation.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +19,12 @@ from gpu_helpers import check_parents, pr_close
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 SEED = 20210404
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rmat22_oracle.json")
+
+
+def golden22():
+    with open(GOLDEN) as f:
+        return json.load(f)
 
 
 @pytest.fixture(scope="module")
@@ -33,24 +42,38 @@ def rmat22():
 
 
 def test_rmat22_bfs_16_sources(L, rmat22):
+    """All 16 bench sources through lagr_bfs_multi (the call bench.py times), every level array
+    against the oracle element by element, every parent array checked; the oracle's depths and
+    level histograms also match the stored golden values."""
     g = rmat22
     G = L.Graph.from_host(g)
-    srcs = gen.sources(g, 16, seed=SEED)
-    assert len(srcs) == 16 and len(set(srcs.tolist())) == 16
+    srcs = [int(s) for s in gen.sources(g, 16, seed=SEED)]
+    assert len(set(srcs)) == 16
+    gold = golden22()
+    assert gold["nnz"] == g.nnz and gold["sources"] == srcs
+    lv, par, depths = L.lagr_bfs_multi(G, srcs)
+    lv = lv.cpu().numpy()
+    par = par.cpu().numpy()
     for i, s in enumerate(srcs):
-        level, parent, depth = L.lagr_bfs(G, int(s))
-        level = level.cpu().numpy()
-        parent = parent.cpu().numpy()
-        if i < 3:  # oracle comparison on a sample of the sources
-            olevel, _, odepth = oracle.bfs(g, int(s))
-            assert np.array_equal(level, olevel) and depth == odepth
-        check_parents(g, level, parent, int(s))
+        olevel, _, odepth = oracle.bfs(g, s)
+        assert odepth == gold["bfs"][i]["depth"]
+        assert np.bincount(olevel[olevel >= 0]).tolist() == gold["bfs"][i]["level_histogram"]
+        assert np.array_equal(lv[i], olevel), i
+        assert depths[i] == odepth
+        check_parents(g, lv[i], par[i], s)
+    # lagr_bfs (one source per call) on a sample, against the same oracle levels
+    for i in (0, 7, 15):
+        level, parent, depth = L.lagr_bfs(G, srcs[i])
+        assert np.array_equal(level.cpu().numpy(), lv[i]) and depth == depths[i]
 
 
-def test_rmat22_tc_invariants(L, rmat22):
+def test_rmat22_tc_golden_and_invariants(L, rmat22):
     g = rmat22
     G = L.Graph.from_host(g)
     t_auto = L.lagr_tc(G, L.LAGR_TC_AUTO)
+    gold = golden22()
+    assert gold["nnz"] == g.nnz
+    assert t_auto == gold["triangles"]  # the oracle's count (Alg. 6 as written, method AUTO)
     assert L.lagr_tc(G, L.LAGR_TC_SORT) == t_auto
     assert oracle.tc_wants_sort(g)[0]          # Alg. 6 sorts this graph
     G.free()
@@ -140,3 +163,6 @@ def test_batch512_matches_plain_calls(L):
         Gi.free()
     for i in range(0, 512, 97):   # oracle on a sample of the members
         assert int(ntri[i]) == oracle.tc(parts[i])
+        ro, ito, _ = oracle.pagerank(parts[i], 0.85, 0.0, 20)
+        assert ito == 20
+        pr_close(rank[b.voff[i]:b.voff[i + 1]], ro)

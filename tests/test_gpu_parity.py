@@ -604,3 +604,25 @@ def test_release_memory_between_graphs(L, rmat12):
         G.free()
         L.lagr_release_memory(keep)
     assert L.lagr_tc(dev(L, rmat12)) == t
+
+
+@pytest.mark.parametrize("which", ["cta", "warp"])
+def test_tc_anchor_list_overflow_is_an_error(L, rmat12, which):
+    """The anchor lists of the triangle count have capacities derived from nnz (a bound that holds
+    on every symmetric graph).  With a capacity forced below what the graph needs (R-MAT 12 on the
+    given labels has 39 CTA items and 17 chunked warp items), the classification skips the writes
+    past the end and the count kernels read no further than the capacity: lagr_tc reports
+    LAGR_ERR_INVALID_GRAPH, and a later call with the computed capacities is exact again."""
+    lib = L.load_library()
+    t = oracle.tc(rmat12, oracle.TC_NOSORT)
+    try:
+        assert lib.lagr_debug_tc_capacity(1 if which == "cta" else 0, 1 if which == "warp" else 0) == 0
+        G = dev(L, rmat12)
+        with pytest.raises(L.LagrError) as e:
+            L.lagr_tc(G, L.LAGR_TC_NOSORT)
+        assert e.value.code == L.LAGR_ERR_INVALID_GRAPH
+    finally:
+        assert lib.lagr_debug_tc_capacity(0, 0) == 0
+    assert L.lagr_tc(G, L.LAGR_TC_NOSORT) == t   # the orientation is rebuilt with full capacities
+    assert L.lagr_tc(dev(L, rmat12), L.LAGR_TC_NOSORT) == t
+    assert lib.lagr_debug_tc_capacity(-1, 0) == L.LAGR_ERR_INVALID_VALUE

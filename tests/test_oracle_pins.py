@@ -237,7 +237,7 @@ def test_bfs_scipy_shortest_path(directed):
 
 
 # ----------------------------------------------------------------------------------------------
-# PageRank (Alg. 3)
+# PageRank (Alg. 4)
 # ----------------------------------------------------------------------------------------------
 
 def dense_pagerank(g, alpha, dangling, W=None, v=None):

@@ -1,9 +1,11 @@
 """lagr_bfs_noalloc: the BFS for callers that cannot allocate device memory.
 
-It must give the same levels as lagr_bfs (exact: levels are integers) and valid parents, on two
-calls in a row (the built-in work array keeps the previous call's contents, so the second call
-checks that everything that must start cleared is cleared), even while every library allocation
-is made to fail.  Runs last (file name) so that a failure here comes after every other test.
+It must give the same levels as lagr_bfs and as the oracle (exact: levels are integers) and valid
+parents, on two calls in a row (the built-in work array keeps the previous call's contents, so the
+second call checks that everything that must start cleared is cleared), even while every library
+allocation is made to fail.  A second graph is chosen so that its traversal takes the wide push
+(the warp-per-vertex kernel that only this entry point uses) and both direction changes.  Runs
+last (file name) so that a failure here comes after every other test.
 """
 import ctypes
 
@@ -11,9 +13,50 @@ import numpy as np
 import pytest
 
 import gen
+import oracle
 from gpu_helpers import check_parents
 
 pytestmark = pytest.mark.gpu
+
+# the direction rule and the narrow-frontier limits of the BFS (Beamer's rule, alpha 14, beta 24;
+# frontiers of at most 8192 vertices and 16384 edges stay in the single-CTA kernel)
+ALPHA, BETA, SMALL_MAX, SMALL_EDGES = 14, 24, 8192, 16384
+
+
+def phases(g, level):
+    """The phases the host loop of the allocation-free BFS takes, replayed on the CPU from the
+    oracle's levels: 'small' (single-CTA push, possibly several levels), 'push' (wide push) or
+    'pull', in order."""
+    deg = np.diff(g.rowptr).astype(np.int64)
+    depth = int(level.max()) + 1
+    nq = np.bincount(level[level >= 0], minlength=depth).astype(np.int64)
+    mfl = np.bincount(level[level >= 0], weights=deg[level >= 0], minlength=depth).astype(np.int64)
+    seen = np.cumsum(mfl)
+    out, pull, prev, lev = [], False, 0, 0
+    while lev < depth and nq[lev] > 0:
+        q, mf, mu = nq[lev], mfl[lev], g.nnz - seen[lev]
+        pull = (q > prev and mf > mu // ALPHA) if not pull else not (q < g.n // BETA)
+        prev = q
+        if pull:
+            out.append("pull")
+            lev += 1
+        elif q <= SMALL_MAX and mf <= SMALL_EDGES:
+            out.append("small")
+            first, grow = True, False
+            while True:  # the single-CTA kernel's own exit rule
+                if lev >= depth or nq[lev] == 0:
+                    break
+                if not first and (nq[lev] > SMALL_MAX or mfl[lev] > SMALL_EDGES):
+                    break
+                if not first and grow and mfl[lev] > (g.nnz - seen[lev]) // ALPHA:
+                    break
+                grow = lev + 1 < depth and nq[lev + 1] > nq[lev]
+                lev += 1
+                first = False
+        else:
+            out.append("push")
+            lev += 1
+    return out
 
 
 def test_noalloc_bfs_matches_lagr_bfs_twice():
@@ -26,6 +69,8 @@ def test_noalloc_bfs_matches_lagr_bfs_twice():
     ci = torch.from_numpy(g.colidx).cuda()
     srcs = [int(s) for s in gen.sources(g, 2, seed=78)]
     expect = [L.lagr_bfs(G, s) for s in srcs]
+    for (lvl, _, _), s in zip(expect, srcs):
+        assert np.array_equal(lvl.cpu().numpy(), oracle.bfs(g, s)[0])
 
     lib = L.load_library()
     alloc_t = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -55,6 +100,31 @@ def test_noalloc_bfs_matches_lagr_bfs_twice():
         assert len(calls) == n_failed          # no allocation was attempted
     finally:
         lib.lagr_set_allocator(None, None, None)
+
+
+def test_noalloc_bfs_wide_push_matches_oracle():
+    """Erdos-Renyi n = 2^20, average degree 8: from a seeded source the frontier grows past the
+    single-CTA limits before the pull pays off, so two levels run the wide push (memset of the next
+    bitmap, warp-per-vertex push, bitmap as the next frontier), then the pull, then push again."""
+    import torch
+    import paper_2104_01661_gb300 as L
+
+    g = gen.erdos_renyi(1 << 20, 8, seed=5)
+    rp = torch.from_numpy(g.rowptr).cuda()
+    ci = torch.from_numpy(g.colidx).cuda()
+    for s in [int(x) for x in gen.sources(g, 2, seed=6)]:
+        olevel, _, odepth = oracle.bfs(g, s)
+        ph = phases(g, olevel)
+        assert ph.count("push") >= 2 and "pull" in ph, ph
+        assert ph.index("pull") < len(ph) - 1, ph  # a pull -> push switch after the pull phase
+        for _ in range(2):  # twice in a row over the stale work array
+            level = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+            parent = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+            depth = L.lagr_bfs_noalloc(rp, ci, s, level, parent)
+            lv = level.cpu().numpy()
+            assert depth == odepth
+            assert np.array_equal(lv, olevel)
+            check_parents(g, lv, parent.cpu().numpy(), s)
 
 
 def test_noalloc_bfs_rejects_oversize_graphs():
