@@ -166,6 +166,10 @@ def run_gpu(args):
     L.load_library()
 
     g = gen.rmat(args.scale, EF, seed=SEED)
+    if args.only == "next":  # profiling case: the next rows alone on this graph (not a bench line)
+        hbm_peak, _ = peaks()
+        return {"config": {"workload": f"profiling case: rmat{args.scale}_ef{EF}, next rows (not a bench line)"},
+                "extras": extras_next_rows(L, dev, hbm_peak, g)} if rank == 0 else None
     srcs = [int(s) for s in gen.sources(g, NSRC, seed=SEED)]
     n, nnz = g.n, g.nnz
     m_und = nnz // 2
@@ -785,7 +789,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-launch-count", action="store_true", help="skip the profiler-based launch count")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--only", default="all", choices=["all", "tc", "bfs", "pr"],
+    ap.add_argument("--only", default="all", choices=["all", "tc", "bfs", "pr", "next"],
                     help="run one component only (profiling captures; not a bench line)")
     ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (profiling captures; not a bench line)")
     ap.add_argument("--no-extras", action="store_true", help="skip the other configurations")

@@ -365,6 +365,167 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1)
   }
 }
 
+// ---- narrow levels on the whole GPU: a cooperative launch with a grid barrier per level --------
+//
+// The single-CTA kernel above keeps narrow levels cheap but runs each level's chain of dependent
+// loads on 1024 threads: on a high-diameter graph (the paper's road graph; the 4096 x 4096 grid
+// here, frontiers of up to 4096 vertices over 8191 levels) a level costs the latency of several
+// such chains.  bfs_push_coop spreads each level over every CTA of a cooperative launch (all CTAs
+// resident at once, so they can wait for each other) and separates the levels with a grid barrier.
+// The barrier's wait is bounded: when it runs out the kernel records LAGR_ERR_TIMEOUT and every
+// CTA leaves.  The frontier is appended to a queue with one counter per level; three counters in
+// rotation let a level reset the counter of the level after next without a second barrier.  The
+// exit rule is that of the single-CTA kernel, with wider limits.
+
+constexpr int COOP_THREADS = 256;
+constexpr int64_t COOP_MAX = 1 << 15;       // frontiers up to this many vertices ...
+constexpr int64_t COOP_EDGES = 1 << 15;     // ... and out-edges stay in the cooperative kernel (a
+                                            // row longer than 8 is one warp's, so this bounds it)
+constexpr int COOP_BIG = 512;               // long rows a CTA lists per level (more: walked inline)
+constexpr long long COOP_SPIN = 1ll << 24;  // barrier polls before giving up (seconds)
+
+struct CoopState {
+  unsigned long long qcount[3], mdeg[3];  // next-frontier size and out-degree sum, per level mod 3
+  unsigned int arrive;                    // grid barrier arrivals (monotone)
+  int err;                                // LAGR_ERR_TIMEOUT when a barrier wait ran out
+};
+
+// returns false when the wait ran out (then st->err is set and every CTA will leave)
+__device__ __forceinline__ bool coop_barrier(CoopState *st, unsigned int target) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&st->arrive, 1u);
+    int ok = 1;
+    long long it = 0;
+    while (*(volatile unsigned int *)&st->arrive < target) {
+      if (*(volatile int *)&st->err || ++it > COOP_SPIN) {
+        ok = 0;
+        atomicExch(&st->err, LAGR_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(COOP_THREADS)
+    bfs_push_coop(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
+                  int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
+                  int32_t *__restrict__ parent, int64_t *__restrict__ c, CoopState *__restrict__ st,
+                  int32_t max_level, int allow_pull, int64_t *hm) {
+  __shared__ int32_t s_big[COOP_BIG];
+  __shared__ int s_nbig;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  int64_t nq = c[B_NQ], mu = c[B_MU], mf = c[B_MF];
+  int32_t lev = (int32_t)c[B_LEV];
+  int par = (int)c[B_PAR];
+  int exit_reason = 0;
+  bool first = true, growing = false;
+  unsigned int bar = 0;
+  for (int it = 0;; it++) {
+    if (nq == 0) { exit_reason = 1; break; }
+    if (!first && (nq > COOP_MAX || mf > COOP_EDGES)) { exit_reason = 2; break; }
+    if (!first && allow_pull && growing && mf > mu / ALPHA_DO) { exit_reason = 3; break; }
+    if (lev + 1 > max_level) { exit_reason = 4; break; }
+    const int nxt = (it + 1) % 3;
+    if (gtid == 0) {  // counters of the level after next: last read a level ago
+      st->qcount[(it + 2) % 3] = 0;
+      st->mdeg[(it + 2) % 3] = 0;
+    }
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
+    const int32_t *qin = par ? qb : qa;
+    int32_t *qout = par ? qa : qb;
+    unsigned long long *qcount = &st->qcount[nxt];
+    unsigned long long mdeg = 0;
+    const int32_t nlev = lev + 1;
+    for (int64_t i = gtid; i < nq; i += gthreads) {
+      const int32_t u = qin[i];
+      const int32_t rs = rowptr[u];
+      int32_t len = rowptr[u + 1] - rs;
+      if (len > NARROW_DEG) {
+        const int b = atomicAdd(&s_nbig, 1);
+        if (b < COOP_BIG) {
+          s_big[b] = u;
+          len = 0;
+        }
+      }
+      // short rows (and long ones past the CTA's list): this thread claims the neighbours itself
+      for (int32_t k = 0; k < len; k++) {
+        const int32_t w = colidx[rs + k];
+        if (claim(visited, w)) {
+          qout[atomicAdd(qcount, 1ull)] = w;
+          if (level) level[w] = nlev;
+          if (parent) parent[w] = u;
+          mdeg += (unsigned long long)(rowptr[w + 1] - rowptr[w]);
+        }
+      }
+    }
+    __syncthreads();
+    // the CTA's long rows: its warps take 32 at a time, edges spread over the lanes
+    const int nb = min(s_nbig, COOP_BIG);
+    for (int wb = (threadIdx.x >> 5) * 32; wb < nb; wb += (int)(blockDim.x >> 5) * 32) {
+      int32_t u = -1, rs = 0, len = 0;
+      if (wb + lane < nb) {
+        u = s_big[wb + lane];
+        rs = rowptr[u];
+        len = rowptr[u + 1] - rs;
+      }
+      warp_segments(rs, len, u, [&](bool valid, int uu, int, int gidx) {
+        bool won = false;
+        int32_t w = 0, dw = 0;
+        if (valid) {
+          w = colidx[gidx];
+          won = claim(visited, w);
+          if (won) dw = rowptr[w + 1] - rowptr[w];
+        }
+        const unsigned m = __ballot_sync(LAGR_FULL_MASK, won);
+        if (m) {
+          unsigned long long pos = 0;
+          if (lane == 0) pos = atomicAdd(qcount, (unsigned long long)__popc(m));
+          pos = __shfl_sync(LAGR_FULL_MASK, pos, 0);
+          if (won) {
+            qout[pos + __popc(m & lt)] = w;
+            if (level) level[w] = nlev;
+            if (parent) parent[w] = uu;
+            mdeg += (unsigned long long)dw;
+          }
+        }
+      });
+    }
+    mdeg = warp_sum(mdeg);
+    if (lane == 0 && mdeg) atomicAdd(&st->mdeg[nxt], mdeg);
+    bar += gridDim.x;
+    if (!coop_barrier(st, bar)) { exit_reason = 5; break; }
+    const int64_t nq_before = nq;
+    nq = (int64_t)*(volatile unsigned long long *)&st->qcount[nxt];
+    mf = (int64_t)*(volatile unsigned long long *)&st->mdeg[nxt];
+    mu -= mf;
+    lev = nlev;
+    par ^= 1;
+    growing = nq > nq_before;
+    first = false;
+  }
+  if (gtid == 0) {
+    c[B_NQ] = nq;
+    c[B_LEV] = lev;
+    c[B_PAR] = par;
+    c[B_MU] = mu;
+    c[B_MF] = mf;
+    c[B_EXIT] = exit_reason;
+    if (hm) mirror_counters(c, hm);
+  }
+}
+
 // queue -> frontier bitmap (the bitmap is cleared first by the caller)
 __global__ void bfs_q2b(const int32_t *__restrict__ qa, const int32_t *__restrict__ qb, const int64_t *__restrict__ c,
                         uint32_t *__restrict__ fbits) {
@@ -737,6 +898,25 @@ using namespace lagr;
 namespace lagr {
 namespace {
 
+// the device can launch cooperative kernels (queried once per device)
+bool coop_supported() {
+  static int cached[64];  // 0 unknown, 1 yes, 2 no
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) {
+    cudaGetLastError();
+    return false;
+  }
+  if (!cached[d]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, d) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    cached[d] = v ? 1 : 2;
+  }
+  return cached[d] == 1;
+}
+
 // One direction-optimising parents BFS (Alg. 1 / 2) as a host-side state machine on its own stream.
 // launch() takes the counters of the last phase from the mapped host mirror h (the phase's last
 // kernel stores them there), applies the direction rule and enqueues the next phase: several
@@ -753,6 +933,8 @@ struct BfsRun {
   Temp<uint32_t> visited, fbits, nbits;
   Temp<int32_t> qa, qb, fdeg, offs;
   Temp<int64_t> cnt;
+  Temp<CoopState> cst;  // the cooperative kernel's counters and barrier (coop runs only)
+  bool coop = false;    // narrow levels on the whole GPU (a run that has the GPU to itself)
   int rep = 0;  // frontier representation: 0 = queue (push), 1 = bitmap fbits (pull)
   int pushes = 0, pulls = 0;
   int32_t last_lev = 0;  // deepest level that discovered a vertex
@@ -763,7 +945,7 @@ struct BfsRun {
   int32_t lev0 = 0;      // the level count before it
 
   explicit BfsRun(cudaStream_t st)
-      : s(st), visited(st), fbits(st), nbits(st), qa(st), qb(st), fdeg(st), offs(st), cnt(st) {}
+      : s(st), visited(st), fbits(st), nbits(st), qa(st), qb(st), fdeg(st), offs(st), cnt(st), cst(st) {}
 
   int start(char *msg) {
     const int32_t n = G->n;
@@ -776,6 +958,7 @@ struct BfsRun {
     LAGR_TRY(fdeg.alloc(n, msg, "frontier degrees"));
     LAGR_TRY(offs.alloc((size_t)n + 1, msg, "frontier edge offsets"));
     LAGR_TRY(cnt.alloc(B_NSLOT, msg, "BFS counters"));
+    if (coop) LAGR_TRY(cst.alloc(1, msg, "cooperative BFS state"));
     bfs_init<<<grid_for(n, 256), 256, 0, s>>>(n, level, parent, visited.p, nwords);
     bfs_seed<<<1, 1, 0, s>>>(G->rowptr, G->nnz, src, level, parent, visited.p, qa.p, cnt.p, hd);
     LAGR_LAUNCH_CHECK();
@@ -812,7 +995,28 @@ struct BfsRun {
         LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p + B_NEXT, 0, sizeof(int64_t), s));
         rep = 0;
       }
-      if (nq <= SMALL_MAX && mf <= SMALL_EDGES) {
+      if (coop && nq <= COOP_MAX && mf <= COOP_EDGES) {
+        // narrow levels on every SM: a cooperative launch (all CTAs resident), one grid barrier
+        // per level, until the frontier widens past the cooperative limits or asks for a pull
+        LAGR_CUDA_TRY(cudaMemsetAsync(cst.p, 0, sizeof(CoopState), s));
+        const int res = resident_ctas((const void *)bfs_push_coop, COOP_THREADS, 0);
+        const int grid = res < 2 * sm_count() ? res : 2 * sm_count();
+        const int32_t *rp = G->rowptr, *ci = G->colidx;
+        int32_t *qap = qa.p, *qbp = qb.p, *lv = level, *pa = parent;
+        uint32_t *vis = visited.p;
+        int64_t *cn = cnt.p, *hm = hd;
+        CoopState *stp = cst.p;
+        int32_t maxl = n;
+        int allow = push_only ? 0 : 1;
+        void *args[] = {&rp, &ci, &qap, &qbp, &vis, &lv, &pa, &cn, &stp, &maxl, &allow, &hm};
+        {
+          KTimer kt(TK_BFS_SMALL, s);
+          LAGR_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)bfs_push_coop, dim3(grid), dim3(COOP_THREADS), args,
+                                                    0, s));
+        }
+        note_launch();
+        phase = 1;
+      } else if (nq <= SMALL_MAX && mf <= SMALL_EDGES) {
         // several narrow levels in one CTA; it stops when the frontier empties, widens, or the
         // direction rule asks for a pull (the same rule as above, so it runs at least one level)
         {
@@ -868,6 +1072,10 @@ struct BfsRun {
       const int32_t levs = (int32_t)h[B_LEV] - lev0;
       if (h[B_EXIT] == 4) {
         set_msg(msg, "BFS exceeded n levels");
+        return LAGR_ERR_TIMEOUT;
+      }
+      if (h[B_EXIT] == 5) {
+        set_msg(msg, "a grid barrier of the cooperative BFS kernel ran out of time");
         return LAGR_ERR_TIMEOUT;
       }
       if (levs <= 0) {
@@ -960,6 +1168,7 @@ extern "C" int lagr_bfs(int32_t *level, int32_t *parent, int32_t *depth, lagr_gr
   r.parent = parent;
   r.push_only = flags & LAGR_BFS_PUSH_ONLY;
   r.pull_only = flags & LAGR_BFS_PULL_ONLY;
+  r.coop = coop_supported();
   r.h = mir.host(0);
   r.hd = mir.dev(0);
   LAGR_TRY(r.start(msg));

@@ -27,6 +27,7 @@ namespace lagr {
 namespace {
 
 constexpr int CC_THREADS = 256;
+constexpr int CC_RUN = 8;  // consecutive entries per thread in the row-block fold
 constexpr int CC_ROUND_CAP_EXTRA = 64;  // rounds allowed beyond 2 log2(n) before giving up
 
 __global__ void cc_init(int32_t n, int32_t *__restrict__ f, int32_t *__restrict__ gf, int32_t *__restrict__ mngf,
@@ -81,14 +82,32 @@ __global__ void __launch_bounds__(CC_THREADS)
   for (int32_t q = threadIdx.x; q <= nr; q += blockDim.x) rp[q] = rowptr[r0 + q];
   for (int32_t q = threadIdx.x; q < nr; q += blockDim.x) rmin[q] = mngf[r0 + q];
   __syncthreads();
+  // each thread folds CC_RUN consecutive entries per pass: one row search for the first, then the
+  // rows advance with the entries, and a row's minimum enters rmin once per run
   const int32_t e0 = rp[0], e1 = rp[nr];
-  for (int32_t k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
-    int32_t lo = 0, hi = nr - 1;  // the row of entry k: the last q with rp[q] <= k
+  for (int32_t k0 = e0 + threadIdx.x * CC_RUN; k0 < e1; k0 += blockDim.x * CC_RUN) {
+    int32_t lo = 0, hi = nr - 1;  // the row of entry k0: the last q with rp[q] <= k0
     while (lo < hi) {
       const int32_t mid = (lo + hi + 1) >> 1;
-      if (rp[mid] <= k) lo = mid; else hi = mid - 1;
+      if (rp[mid] <= k0) lo = mid; else hi = mid - 1;
     }
-    atomicMin(&rmin[lo], __ldg(&gf[__ldg(&colidx[k])]));
+    const int32_t kend = min(e1, k0 + CC_RUN);
+    int32_t g[CC_RUN];
+#pragma unroll
+    for (int j = 0; j < CC_RUN; j++) g[j] = k0 + j < kend ? __ldg(&gf[__ldg(&colidx[k0 + j])]) : INT_MAX;
+    int32_t q = lo, m = INT_MAX, rend = rp[lo + 1];
+#pragma unroll
+    for (int j = 0; j < CC_RUN; j++) {
+      if (k0 + j >= kend) break;
+      while (k0 + j >= rend) {  // the row ended: fold its part, step over empty rows
+        if (m != INT_MAX) atomicMin(&rmin[q], m);
+        m = INT_MAX;
+        q++;
+        rend = rp[q + 1];
+      }
+      m = min(m, g[j]);
+    }
+    if (m != INT_MAX) atomicMin(&rmin[q], m);
   }
   __syncthreads();
   for (int32_t q = threadIdx.x; q < nr; q += blockDim.x) {

@@ -27,6 +27,8 @@ void set_msg(char *msg, const char *fmt, ...) {
 
 static unsigned long long g_launches = 0;
 
+void note_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+
 }  // namespace lagr
 
 extern "C" cudaError_t __real___cudaLaunchKernel(cudaKernel_t kernel, dim3 grid, dim3 block, void **args,

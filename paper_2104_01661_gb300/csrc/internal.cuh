@@ -192,6 +192,8 @@ int resident_ctas(const void *kernel, int threads, size_t smem);
 // grid of a grid-stride kernel over `work` items: one CTA per `threads` items, at most `waves`
 // CTAs per multiprocessor
 int grid_for(int64_t work, int threads, int waves = 16);
+// count a launch that does not go through <<<...>>> (a cooperative launch) in lagr_kernel_launches
+void note_launch();
 
 // validation shared by the entry points
 int check_graph_arg(lagr_graph G, char *msg);

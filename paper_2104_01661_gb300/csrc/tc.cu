@@ -748,38 +748,63 @@ __global__ void __launch_bounds__(TCC_THREADS)
 //
 // C(i,j) at an entry of L (rank i > rank j) counts the k with j < k < i adjacent to both, i.e. the
 // k in U(j) whose own list U(k) holds i.  So the lowest vertex j of each triangle is the anchor:
-// its list U(j) goes into a hash table keyed by rank with a counter per key, every list U(k) of a
-// k in U(j) is probed against it, and a hit on key i counts one triangle (j, k, i) for C(i, j).
-// The counts are then written to the stored entry (i, j) of A (row i, found by binary search).
-// Every anchor owns its table, so the counts are exact; their sum is t.  Anchors with d+ <= 256
-// run one per warp (a 512-slot table in shared memory), those up to KEPT_CTA_MAXD one per CTA
-// (the table in shared memory), longer ones one per CTA with the table in global memory.
+// the entries of its row A(j,:) that rank above j go into a hash table keyed by rank, each slot
+// holding the entry's position in the CSR and a counter; every list U(k) of such a k is probed
+// against it, and a hit on key i counts one triangle (j, k, i) for C(i, j).  The anchor then writes
+// its counts to the positions of its own entries (j, i) -- the U side; a second pass moves each
+// value to the mirror entry (i, j) on the L side (found by binary search in the lower vertex's
+// row j, short after the degree ordering) and clears the U side.  Every anchor owns its table, so
+// the counts are exact; their sum is t.  Anchors with d+ <= 256 run one per warp (a 512-slot
+// table in shared memory), those up to KEPT_CTA_MAXD one per CTA (the table in shared memory),
+// longer ones one per CTA with the table in global memory.
 
 constexpr int KEPT_WSLOTS = 512;
 constexpr int KEPT_WMAXD = KEPT_WSLOTS / 2;
-constexpr int KEPT_CTA_MAXD = 8192;
+constexpr int KEPT_CTA_MAXD = 4096;
 constexpr int KEPT_THREADS = 256;
+constexpr int KEPT_WWARPS = 4;                     // warps per CTA of the warp-anchor kernel
 constexpr int KEPT_SLOTS_MAX = 2 * KEPT_CTA_MAXD;  // table slots of the largest shared-memory table
-enum KeptSlot { KS_NW = 0, KS_NC = 1, KS_NH = 2, KS_QW = 3, KS_QC = 4, KS_QH = 5, KS_TOTAL = 6, KS_HSLOTS = 7,
-                KS_NSLOT = 8 };
+enum KeptSlot { KS_NW = 0, KS_NC = 1, KS_NH = 2, KS_QW = 3, KS_QC = 4, KS_QH = 5, KS_TOTAL = 6, KS_NSLOT = 8 };
 
-__device__ __forceinline__ int hfind(const int32_t *tab, int logT, int32_t w) {
-  const uint32_t mask = (1u << logT) - 1;
-  uint32_t h = hslot(w, logT);
-  for (uint32_t i = 0; i <= mask; i++) {
-    const int32_t v = tab[h];
-    if (v == w) return (int)h;
-    if (v == EMPTY) return -1;
-    h = (h + 1) & mask;
+// a counting table: keys (ranks), the CSR position of each key's entry, a counter.  The table may
+// live in global memory, where its keys and counters change by atomics (performed at L2) while
+// earlier plain loads may have left the lines in L1: every read is a volatile load, which does not
+// use L1.
+__device__ __forceinline__ int32_t vload(const int32_t *p) { return *(const volatile int32_t *)p; }
+__device__ __forceinline__ uint32_t vload(const uint32_t *p) { return *(const volatile uint32_t *)p; }
+
+struct KeptTable {
+  int32_t *key, *pos;
+  uint32_t *cnt;
+  int logT;
+  bool global;  // the table is in global memory (reads bypass L1)
+  __device__ __forceinline__ int32_t rkey(int h) const { return global ? vload(&key[h]) : key[h]; }
+  __device__ __forceinline__ void insert(int32_t r, int32_t p) const {
+    const uint32_t mask = (1u << logT) - 1;
+    uint32_t h = hslot(r, logT);
+    // at least twice as many slots as keys: a free slot exists; the bound only ends the loop
+    for (uint32_t i = 0; i <= mask; i++) {
+      if (atomicCAS(&key[h], EMPTY, r) == EMPTY) {
+        pos[h] = p;
+        return;
+      }
+      h = (h + 1) & mask;
+    }
   }
-  return -1;
-}
-
-// rank -> vertex id
-__global__ void tc_rank_inverse(const int32_t *__restrict__ rank, int32_t n, int32_t *__restrict__ inv) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    inv[rank[i]] = (int32_t)i;
-}
+  __device__ __forceinline__ void count(int32_t r) const {
+    const uint32_t mask = (1u << logT) - 1;
+    uint32_t h = hslot(r, logT);
+    for (uint32_t i = 0; i <= mask; i++) {
+      const int32_t k = rkey((int)h);
+      if (k == r) {
+        atomicAdd(&cnt[h], 1u);
+        return;
+      }
+      if (k == EMPTY) return;
+      h = (h + 1) & mask;
+    }
+  }
+};
 
 // the anchors by class; the global tables of the longest ones get their slot counts in hsz
 __global__ void tc_kept_classify(const int32_t *__restrict__ dplus, int32_t n, int32_t *__restrict__ lw,
@@ -800,61 +825,71 @@ __global__ void tc_kept_classify(const int32_t *__restrict__ dplus, int32_t n, i
   }
 }
 
-// One anchor v, processed by `ng` warps of a group (warp index gw within it) with the table
-// (keys, cnt) of 2^logT slots; sync() is the group's barrier.  Writes the anchor's C values into c
-// and adds their sum into *total.
+// One anchor v, processed by `ng` warps of a group (warp index gw within it) with the table t;
+// sync() is the group's barrier.  Writes the anchor's counts to the positions of its U entries in
+// c (cleared before the pass) and adds their sum into *total.
 template <class Sync>
 __device__ __forceinline__ void kept_anchor(int32_t v, const int32_t *__restrict__ rowptr,
                                             const int32_t *__restrict__ colidx, const int32_t *__restrict__ dplus,
-                                            const int32_t *__restrict__ u_colidx, const int32_t *__restrict__ inv,
-                                            int32_t *keys, uint32_t *cnt, int logT, int gw, int ng, int gtid,
-                                            int gsize, Sync &&sync, uint32_t *__restrict__ c,
-                                            unsigned long long *__restrict__ total) {
+                                            const int32_t *__restrict__ u_colidx, const int32_t *__restrict__ rank,
+                                            const KeptTable &t, int gw, int ng, int gtid, int gsize, Sync &&sync,
+                                            uint32_t *__restrict__ c, unsigned long long *__restrict__ total) {
   const int lane = threadIdx.x & 31;
-  const int32_t a = dplus[v];
-  const int32_t ub = rowptr[v];
-  const int T = 1 << logT;
+  const int32_t rv = rank[v];
+  const int32_t b = rowptr[v], e = rowptr[v + 1];
+  const int T = 1 << t.logT;
   for (int i = gtid; i < T; i += gsize) {
-    keys[i] = EMPTY;
-    cnt[i] = 0u;
+    t.key[i] = EMPTY;
+    t.cnt[i] = 0u;
   }
   sync();
-  for (int i = gtid; i < a; i += gsize) hinsert(keys, logT, u_colidx[ub + i]);
+  for (int32_t p = b + gtid; p < e; p += gsize) {
+    const int32_t r = rank[colidx[p]];
+    if (r > rv) t.insert(r, p);
+  }
   sync();
-  // the middle vertices k in U(v), 32 per warp batch: probe every entry of U(k) against U(v)
-  for (int32_t jb = gw * 32; jb < a; jb += ng * 32) {
+  // the middle vertices k (entries of A(v,:) ranked above v), 32 row entries per warp batch: every
+  // entry of U(k) is probed.  Lists of 32 or more are walked by the whole warp, shorter ones by the
+  // load-balanced segment walk.
+  for (int32_t jb = b + gw * 32; jb < e; jb += ng * 32) {
     const int32_t j = jb + lane;
     int32_t st = 0, len = 0;
-    if (j < a) {
-      const int32_t k = inv[u_colidx[ub + j]];
-      st = rowptr[k];
-      len = dplus[k];
-    }
-    warp_segments(st, len, 0, [&](bool valid, int, int, int gidx) {
-      if (valid) {
-        const int slot = hfind(keys, logT, u_colidx[gidx]);
-        if (slot >= 0) atomicAdd(&cnt[slot], 1u);
+    if (j < e) {
+      const int32_t k = colidx[j];
+      if (rank[k] > rv) {
+        st = rowptr[k];
+        len = dplus[k];
       }
+    }
+    unsigned longs = __ballot_sync(LAGR_FULL_MASK, len >= 32);
+    warp_segments(st, len >= 32 ? 0 : len, 0, [&](bool valid, int, int, int gidx) {
+      if (valid) t.count(u_colidx[gidx]);
     });
+    while (longs) {
+      const int sl = __ffs(longs) - 1;
+      longs &= longs - 1;
+      const int32_t st_s = __shfl_sync(LAGR_FULL_MASK, st, sl), len_s = __shfl_sync(LAGR_FULL_MASK, len, sl);
+      int32_t q = lane;
+      for (; q + 96 < len_s; q += 128) {  // four loads per lane in flight
+        const int32_t w0 = u_colidx[st_s + q], w1 = u_colidx[st_s + q + 32], w2 = u_colidx[st_s + q + 64],
+                      w3 = u_colidx[st_s + q + 96];
+        t.count(w0);
+        t.count(w1);
+        t.count(w2);
+        t.count(w3);
+      }
+      for (; q < len_s; q += 32) t.count(u_colidx[st_s + q]);
+    }
   }
   sync();
-  // C(i, v) for every i in U(v), into the entry (i, v) of A
+  // the anchor's counts at the positions of its entries (v, i)
   unsigned long long mine = 0;
   for (int q = gtid; q < T; q += gsize) {
-    const int32_t r = keys[q];
-    if (r == EMPTY) continue;
-    const uint32_t cv = cnt[q];
+    if (t.rkey(q) == EMPTY) continue;
+    const uint32_t cv = t.global ? vload(&t.cnt[q]) : t.cnt[q];
     if (cv == 0) continue;  // c is cleared before the pass
-    const int32_t top = inv[r];
-    int32_t lo = rowptr[top], hi = rowptr[top + 1];
-    while (lo < hi) {
-      const int32_t mid = lo + ((hi - lo) >> 1);
-      if (colidx[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    if (lo < rowptr[top + 1] && colidx[lo] == v) {  // present on a symmetric graph
-      c[lo] = cv;
-      mine += cv;
-    }
+    c[t.global ? vload(&t.pos[q]) : t.pos[q]] = cv;
+    mine += cv;
   }
   mine = warp_sum(mine);
   if (lane == 0 && mine) atomicAdd(total, mine);
@@ -862,13 +897,14 @@ __device__ __forceinline__ void kept_anchor(int32_t v, const int32_t *__restrict
 }
 
 // warp-class anchors: one per warp, table in shared memory
-__global__ void __launch_bounds__(KEPT_THREADS)
+__global__ void __launch_bounds__(KEPT_WWARPS * 32)
     tc_kept_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                  const int32_t *__restrict__ dplus, const int32_t *__restrict__ u_colidx,
-                 const int32_t *__restrict__ inv, const int32_t *__restrict__ list, int64_t *__restrict__ ks,
+                 const int32_t *__restrict__ rank, const int32_t *__restrict__ list, int64_t *__restrict__ ks,
                  uint32_t *__restrict__ c) {
-  __shared__ int32_t skeys[KEPT_THREADS / 32][KEPT_WSLOTS];
-  __shared__ uint32_t scnt[KEPT_THREADS / 32][KEPT_WSLOTS];
+  __shared__ int32_t skey[KEPT_WWARPS][KEPT_WSLOTS];
+  __shared__ int32_t spos[KEPT_WWARPS][KEPT_WSLOTS];
+  __shared__ uint32_t scnt[KEPT_WWARPS][KEPT_WSLOTS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nl = ks[KS_NW];
   for (;;) {
@@ -877,19 +913,20 @@ __global__ void __launch_bounds__(KEPT_THREADS)
     it = __shfl_sync(LAGR_FULL_MASK, it, 0);
     if (it >= nl) break;
     const int32_t v = list[it];
-    kept_anchor(v, rowptr, colidx, dplus, u_colidx, inv, skeys[warp], scnt[warp], ceil_log2(2 * dplus[v]), 0, 1,
-                lane, 32, [] { __syncwarp(); }, c, (unsigned long long *)&ks[KS_TOTAL]);
+    const KeptTable t{skey[warp], spos[warp], scnt[warp], ceil_log2(2 * dplus[v]), false};
+    kept_anchor(v, rowptr, colidx, dplus, u_colidx, rank, t, 0, 1, lane, 32, [] { __syncwarp(); }, c,
+                (unsigned long long *)&ks[KS_TOTAL]);
   }
 }
 
-// CTA-class anchors (table in dynamic shared memory) or, with gkeys != NULL, the longest anchors
-// (table at gkeys + hoff[i] in global memory)
+// CTA-class anchors (table in dynamic shared memory) or, with gkey != NULL, the longest anchors
+// (table at offset hoff[i] of the global arrays)
 __global__ void __launch_bounds__(KEPT_THREADS)
     tc_kept_cta(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                 const int32_t *__restrict__ dplus, const int32_t *__restrict__ u_colidx,
-                const int32_t *__restrict__ inv, const int32_t *__restrict__ list, int64_t *__restrict__ ks,
-                int slot_n, int slot_q, int32_t *__restrict__ gkeys, uint32_t *__restrict__ gcnt,
-                const int32_t *__restrict__ hoff, uint32_t *__restrict__ c) {
+                const int32_t *__restrict__ rank, const int32_t *__restrict__ list, int64_t *__restrict__ ks,
+                int slot_n, int slot_q, int32_t *__restrict__ gkey, int32_t *__restrict__ gpos,
+                uint32_t *__restrict__ gcnt, const int32_t *__restrict__ hoff, uint32_t *__restrict__ c) {
   extern __shared__ int32_t ksm[];
   __shared__ long long s_it;
   const int64_t nl = ks[slot_n];
@@ -900,11 +937,57 @@ __global__ void __launch_bounds__(KEPT_THREADS)
     __syncthreads();
     if (it >= nl) break;
     const int32_t v = list[it];
-    const int logT = ceil_log2(2 * dplus[v]);
-    int32_t *keys = gkeys ? gkeys + hoff[it] : ksm;
-    uint32_t *cnt = gkeys ? gcnt + hoff[it] : reinterpret_cast<uint32_t *>(ksm + KEPT_SLOTS_MAX);
-    kept_anchor(v, rowptr, colidx, dplus, u_colidx, inv, keys, cnt, logT, threadIdx.x >> 5, blockDim.x >> 5,
-                threadIdx.x, blockDim.x, [] { __syncthreads(); }, c, (unsigned long long *)&ks[KS_TOTAL]);
+    KeptTable t;
+    t.logT = ceil_log2(2 * dplus[v]);
+    t.global = gkey != nullptr;
+    if (gkey) {
+      t.key = gkey + hoff[it];
+      t.pos = gpos + hoff[it];
+      t.cnt = gcnt + hoff[it];
+    } else {
+      t.key = ksm;
+      t.pos = ksm + KEPT_SLOTS_MAX;
+      t.cnt = reinterpret_cast<uint32_t *>(ksm + 2 * KEPT_SLOTS_MAX);
+    }
+    kept_anchor(v, rowptr, colidx, dplus, u_colidx, rank, t, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x,
+                blockDim.x, [] { __syncthreads(); }, c, (unsigned long long *)&ks[KS_TOTAL]);
+  }
+}
+
+// The counts sit at the U side (v, i); move each to the mirror entry (i, v) of L.  One thread per
+// entry of L: the mirror is in the row of the lower vertex.  A second pass clears the U side.
+__global__ void tc_kept_mirror(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                               const int32_t *__restrict__ rank, const int32_t *__restrict__ blk, int32_t nblk,
+                               uint32_t *__restrict__ c, int clear) {
+  // one CTA per row block of the plan; entries walked in order, rows found in staged pointers
+  __shared__ int32_t rp[ROW_UNITS + 1];
+  for (int32_t bb = blockIdx.x; bb < nblk; bb += gridDim.x) {
+    const int32_t r0 = blk[bb], r1 = blk[bb + 1];
+    const int32_t nr = r1 - r0;
+    __syncthreads();
+    for (int32_t q = threadIdx.x; q <= nr; q += blockDim.x) rp[q] = rowptr[r0 + q];
+    __syncthreads();
+    const int32_t e0 = rp[0], e1 = rp[nr];
+    for (int32_t k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
+      int32_t lo = 0, hi = nr - 1;  // the row of entry k
+      while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (rp[mid] <= k) lo = mid; else hi = mid - 1;
+      }
+      const int32_t i = r0 + lo, j = colidx[k];
+      const bool in_l = rank[i] > rank[j];
+      if (clear) {
+        if (!in_l) c[k] = 0u;
+        continue;
+      }
+      if (!in_l) continue;
+      int32_t a = rowptr[j], z = rowptr[j + 1];  // (j, i) in row j
+      while (a < z) {
+        const int32_t mid = a + ((z - a) >> 1);
+        if (colidx[mid] < i) a = mid + 1; else z = mid;
+      }
+      c[k] = (a < rowptr[j + 1] && colidx[a] == i) ? c[a] : 0u;
+    }
   }
 }
 
@@ -1128,9 +1211,9 @@ extern "C" int lagr_tc_edges(uint32_t *c, uint64_t *ntriangles, lagr_graph G, in
     LAGR_TRY(tc_launch(G, P, method, prm, nullptr, 1, tc_total_slot(P), true, s, msg, false));
     G->u_order = method;
   }
-  Temp<int32_t> inv(s), lw(s), lc(s), lh(s), hsz(s), hoff(s);
+  const RowPlan &rp = P->pr_at;  // built by tc_alloc
+  Temp<int32_t> lw(s), lc(s), lh(s), hsz(s), hoff(s);
   Temp<int64_t> ks(s);
-  LAGR_TRY(inv.alloc(n, msg, "rank inverse"));
   LAGR_TRY(lw.alloc(n, msg, "warp anchors"));
   LAGR_TRY(lc.alloc(n, msg, "CTA anchors"));
   LAGR_TRY(lh.alloc(n, msg, "long anchors"));
@@ -1139,34 +1222,37 @@ extern "C" int lagr_tc_edges(uint32_t *c, uint64_t *ntriangles, lagr_graph G, in
   LAGR_TRY(ks.alloc(KS_NSLOT, msg, "counters"));
   LAGR_CUDA_TRY(cudaMemsetAsync(ks.p, 0, KS_NSLOT * sizeof(int64_t), s));
   LAGR_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)nnz * sizeof(uint32_t), s));
-  tc_rank_inverse<<<grid_for(n, 256), 256, 0, s>>>(P->tc_rank, n, inv.p);
   tc_kept_classify<<<grid_for(n, 256), 256, 0, s>>>(G->u_dplus, n, lw.p, lc.p, lh.p, hsz.p, ks.p);
   LAGR_LAUNCH_CHECK();
   int64_t h[KS_NSLOT];
   LAGR_TRY(fetch_to_host(h, ks.p, sizeof(h), s, msg));
   const int64_t nh = h[KS_NH];
-  Temp<int32_t> gkeys(s);
+  Temp<int32_t> gkey(s), gpos(s);
   Temp<uint32_t> gcnt(s);
   if (nh > 0) {  // global tables of the longest anchors: one after the other
     LAGR_TRY(exclusive_scan(hsz.p, hoff.p, nh, s, msg));
     int32_t tot = 0;
     const int32_t *src[1] = {hoff.p + nh};
     LAGR_TRY(fetch_i32s(&tot, src, 1, s, msg));
-    LAGR_TRY(gkeys.alloc(tot, msg, "anchor tables"));
+    LAGR_TRY(gkey.alloc(tot, msg, "anchor tables"));
+    LAGR_TRY(gpos.alloc(tot, msg, "anchor positions"));
     LAGR_TRY(gcnt.alloc(tot, msg, "anchor counters"));
   }
-  const size_t csmem = (size_t)2 * KEPT_SLOTS_MAX * sizeof(int32_t);
+  const size_t csmem = (size_t)3 * KEPT_SLOTS_MAX * sizeof(int32_t);
   LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_kept_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
   if (h[KS_NW] > 0)
-    tc_kept_warp<<<resident_ctas((const void *)tc_kept_warp, KEPT_THREADS, 0), KEPT_THREADS, 0, s>>>(
-        G->rowptr, G->colidx, G->u_dplus, G->u_colidx, inv.p, lw.p, ks.p, c);
+    tc_kept_warp<<<resident_ctas((const void *)tc_kept_warp, KEPT_WWARPS * 32, 0), KEPT_WWARPS * 32, 0, s>>>(
+        G->rowptr, G->colidx, G->u_dplus, G->u_colidx, P->tc_rank, lw.p, ks.p, c);
   if (h[KS_NC] > 0)
     tc_kept_cta<<<resident_ctas((const void *)tc_kept_cta, KEPT_THREADS, csmem), KEPT_THREADS, csmem, s>>>(
-        G->rowptr, G->colidx, G->u_dplus, G->u_colidx, inv.p, lc.p, ks.p, KS_NC, KS_QC, nullptr, nullptr, nullptr,
-        c);
+        G->rowptr, G->colidx, G->u_dplus, G->u_colidx, P->tc_rank, lc.p, ks.p, KS_NC, KS_QC, nullptr, nullptr,
+        nullptr, nullptr, c);
   if (nh > 0)
-    tc_kept_cta<<<sm_count(), KEPT_THREADS, 0, s>>>(G->rowptr, G->colidx, G->u_dplus, G->u_colidx, inv.p, lh.p,
-                                                    ks.p, KS_NH, KS_QH, gkeys.p, gcnt.p, hoff.p, c);
+    tc_kept_cta<<<sm_count(), KEPT_THREADS, 0, s>>>(G->rowptr, G->colidx, G->u_dplus, G->u_colidx, P->tc_rank,
+                                                    lh.p, ks.p, KS_NH, KS_QH, gkey.p, gpos.p, gcnt.p, hoff.p, c);
+  const int mg = resident_ctas((const void *)tc_kept_mirror, 256, 0);
+  tc_kept_mirror<<<mg, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, rp.nblk, c, 0);
+  tc_kept_mirror<<<mg, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, rp.nblk, c, 1);
   LAGR_LAUNCH_CHECK();
   LAGR_TRY(fetch_to_host(h, ks.p, sizeof(h), s, msg));
   if (ntriangles) *ntriangles = (uint64_t)h[KS_TOTAL];
