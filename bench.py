@@ -166,6 +166,20 @@ def run_gpu(args):
     L.load_library()
 
     g = gen.rmat(args.scale, EF, seed=SEED)
+    if args.only == "adjoint":  # profiling case: weighted PageRank forward and adjoint (not a bench line)
+        gw = gen.rmat_weighted_directed(args.scale, EF, seed=SEED)
+        Gw = L.Graph.from_host(gw)
+        c = torch.from_numpy(gen.normal(gw.n, SEED).astype(np.float32)).to(dev)
+        res = {}
+        for _ in range(max(1, args.steps)):
+            r, it_f = L.lagr_pagerank(Gw, DAMPING, 0.0, 20, flags=L.LAGR_PR_WEIGHTED)
+            _, _, it_b = L.lagr_pagerank_backward(Gw, c, r, DAMPING, 0.0, 20)
+            res = {"forward_iters": it_f, "adjoint_iters": it_b}
+        torch.cuda.synchronize()
+        Gw.free()
+        return {"config": {"workload": f"profiling case: rmat{args.scale}_ef{EF} directed weighted, "
+                           "20 forward + 20 adjoint iterations (not a bench line)"}, "result": res} \
+            if rank == 0 else None
     if args.only == "next":  # profiling case: the next rows alone on this graph (not a bench line)
         hbm_peak, _ = peaks()
         return {"config": {"workload": f"profiling case: rmat{args.scale}_ef{EF}, next rows (not a bench line)"},
@@ -731,11 +745,19 @@ def cpu_sample(g, srcs, budget_s=20.0):
 def host_cpu():
     """(CPU model, logical CPUs) of this host, for the baseline line."""
     model = None
+    try:  # lscpu names Arm cores ("Neoverse-V2"), which /proc/cpuinfo only gives as part numbers
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                if not model and key in ("model name", "cpu model", "hardware") and ":" in line:
                     model = line.split(":", 1)[1].strip()
                     break
     except OSError:
@@ -789,7 +811,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-launch-count", action="store_true", help="skip the profiler-based launch count")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--only", default="all", choices=["all", "tc", "bfs", "pr", "next"],
+    ap.add_argument("--only", default="all", choices=["all", "tc", "bfs", "pr", "next", "adjoint"],
                     help="run one component only (profiling captures; not a bench line)")
     ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (profiling captures; not a bench line)")
     ap.add_argument("--no-extras", action="store_true", help="skip the other configurations")

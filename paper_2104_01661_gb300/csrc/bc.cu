@@ -161,6 +161,47 @@ __global__ void __launch_bounds__(BC_THREADS)
   }
 }
 
+// The same pull for at most NS sources: each lane keeps one running sum per source over the chunk's
+// edges in registers, and the warp reduces each source once per chunk instead of once per 32 edges.
+template <int NS>
+__global__ void __launch_bounds__(BC_THREADS)
+    bc_pull_few(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t ns,
+                const int32_t *__restrict__ lvert, const unsigned long long *__restrict__ lmask, int32_t nent,
+                const int32_t *__restrict__ off, const unsigned long long *__restrict__ dmask,
+                const double *__restrict__ W, double *__restrict__ acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t total = nent > 0 ? off[nent] : 0;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nwarps) {
+    const int32_t i = fx_entry_of(off, nent, (int32_t)c);
+    const int32_t u = lvert[i];
+    const unsigned long long mu = lmask[i];
+    const int32_t b = rowptr[u] + ((int32_t)c - off[i]) * FX_CHUNK;
+    const int32_t e = min(rowptr[u + 1], b + FX_CHUNK);
+    double a[NS];
+#pragma unroll
+    for (int q = 0; q < NS; q++) a[q] = 0.0;
+    unsigned touched = 0;  // the sources this lane has a term for
+    for (int32_t k = b + lane; k < e; k += 32) {
+      const int32_t l = __ldg(&colidx[k]);
+      const unsigned mm = (unsigned)(mu & dmask[l]);
+      touched |= mm;
+#pragma unroll
+      for (int q = 0; q < NS; q++)
+        if ((mm >> q) & 1u) a[q] += W[(int64_t)l * ns + q];
+    }
+    const unsigned any = __reduce_or_sync(LAGR_FULL_MASK, touched);
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+      if (!((any >> q) & 1u)) continue;
+      double t = a[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(LAGR_FULL_MASK, t, o);
+      if (lane == 0) atomicAdd(&acc[(int64_t)u * ns + q], t);
+    }
+  }
+}
+
 // B += W .* P on level d-1 (W there is the pulled sum in acc, cleared here); level d's dense masks
 // are cleared by the caller's second call with clear_only
 __global__ void bc_level_apply(int32_t ns, const int32_t *__restrict__ lvert,
@@ -265,6 +306,8 @@ extern "C" int lagr_betweenness(double *centrality, int32_t *levels, lagr_graph 
   std::vector<int64_t> start = {0, h[BC_NNEXT]};  // level d's list is [start[d], start[d+1])
   const int grid = resident_ctas((const void *)bc_push, BC_THREADS, 0);
   const int pgrid = resident_ctas((const void *)bc_pull, BC_THREADS, 0);
+  const int pgrid4 = resident_ctas((const void *)bc_pull_few<4>, BC_THREADS, 0);
+  const int pgrid8 = resident_ctas((const void *)bc_pull_few<8>, BC_THREADS, 0);
   // BFS phase
   for (int32_t d = 0;; d++) {
     if (d > n) {
@@ -306,8 +349,15 @@ extern "C" int lagr_betweenness(double *centrality, int32_t *levels, lagr_graph 
     bc_level_w<<<grid_for(nd, BC_THREADS), BC_THREADS, 0, s>>>(ns, lv.p + sd, lm.p + sd, (int32_t)nd, B.p,
                                                                sigma.p, W.p, dmask.p);
     LAGR_TRY(fx_plan(&fx, lv.p + su, (int32_t)nu, G->rowptr, s, msg));
-    bc_pull<<<pgrid, BC_THREADS, 0, s>>>(G->rowptr, G->colidx, ns, lv.p + su, lm.p + su, (int32_t)nu, fx.off,
-                                         dmask.p, W.p, acc.p);
+    if (ns <= 4)
+      bc_pull_few<4><<<pgrid4, BC_THREADS, 0, s>>>(G->rowptr, G->colidx, ns, lv.p + su, lm.p + su, (int32_t)nu,
+                                                   fx.off, dmask.p, W.p, acc.p);
+    else if (ns <= 8)
+      bc_pull_few<8><<<pgrid8, BC_THREADS, 0, s>>>(G->rowptr, G->colidx, ns, lv.p + su, lm.p + su, (int32_t)nu,
+                                                   fx.off, dmask.p, W.p, acc.p);
+    else
+      bc_pull<<<pgrid, BC_THREADS, 0, s>>>(G->rowptr, G->colidx, ns, lv.p + su, lm.p + su, (int32_t)nu, fx.off,
+                                           dmask.p, W.p, acc.p);
     bc_level_apply<<<grid_for(nu, BC_THREADS), BC_THREADS, 0, s>>>(ns, lv.p + su, lm.p + su, (int32_t)nu, sigma.p,
                                                                    acc.p, B.p);
     bc_clear_masks<<<grid_for(nd, BC_THREADS), BC_THREADS, 0, s>>>(lv.p + sd, (int32_t)nd, dmask.p);

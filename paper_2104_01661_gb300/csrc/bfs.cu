@@ -308,13 +308,14 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Many narrow push levels in one CTA.  Returns when the frontier is empty, grows past SMALL_MAX
-// vertices or SMALL_EDGES out-edges, the direction rule asks for a pull, or max_level is reached.
+// Many narrow push levels in one CTA.  Returns when the frontier is empty, grows past nmax (at most
+// SMALL_MAX) vertices or SMALL_EDGES out-edges, the direction rule asks for a pull, or max_level is
+// reached.
 __global__ void __launch_bounds__(SMALL_THREADS, 1)
     bfs_push_small(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
                    int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
                    int32_t *__restrict__ parent, int64_t *__restrict__ c, int32_t max_level, int allow_pull,
-                   int64_t *hm) {
+                   int64_t *hm, int64_t nmax = SMALL_MAX) {
   __shared__ unsigned long long s_next, s_mdeg;
   __shared__ int32_t s_big[SMALL_MAX];  // frontier vertices with long rows (the caller keeps nq <= SMALL_MAX)
   __shared__ int s_nbig;
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1)
   for (;;) {
     if (nq == 0) { exit_reason = 1; break; }
     // the caller hands over only narrow frontiers; a level that widens goes back to the grid
-    if (!first && (nq > SMALL_MAX || mf > SMALL_EDGES)) { exit_reason = 2; break; }
+    if (!first && (nq > nmax || mf > SMALL_EDGES)) { exit_reason = 2; break; }
     // the caller chose push for the first level; afterwards pull when a growing frontier's
     // edges outweigh the unexplored edges / alpha
     if (!first && allow_pull && growing && mf > mu / ALPHA_DO) { exit_reason = 3; break; }
@@ -378,6 +379,10 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1)
 // exit rule is that of the single-CTA kernel, with wider limits.
 
 constexpr int COOP_THREADS = 256;
+constexpr int64_t COOP_MIN = 2048;          // frontiers from this many vertices (hysteresis: down
+                                            // to half of it) use the cooperative kernel, below it
+                                            // the single-CTA one (a grid barrier costs more than a
+                                            // level of a few vertices per thread)
 constexpr int64_t COOP_MAX = 1 << 15;       // frontiers up to this many vertices ...
 constexpr int64_t COOP_EDGES = 1 << 15;     // ... and out-edges stay in the cooperative kernel (a
                                             // row longer than 8 is one warp's, so this bounds it)
@@ -414,7 +419,7 @@ __device__ __forceinline__ bool coop_barrier(CoopState *st, unsigned int target)
   return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(COOP_THREADS)
+__global__ void __launch_bounds__(COOP_THREADS, 2)
     bfs_push_coop(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, int32_t *__restrict__ qa,
                   int32_t *__restrict__ qb, uint32_t *__restrict__ visited, int32_t *__restrict__ level,
                   int32_t *__restrict__ parent, int64_t *__restrict__ c, CoopState *__restrict__ st,
@@ -434,6 +439,7 @@ __global__ void __launch_bounds__(COOP_THREADS)
   for (int it = 0;; it++) {
     if (nq == 0) { exit_reason = 1; break; }
     if (!first && (nq > COOP_MAX || mf > COOP_EDGES)) { exit_reason = 2; break; }
+    if (!first && nq < COOP_MIN / 2) { exit_reason = 6; break; }  // narrow again: one CTA does better
     if (!first && allow_pull && growing && mf > mu / ALPHA_DO) { exit_reason = 3; break; }
     if (lev + 1 > max_level) { exit_reason = 4; break; }
     const int nxt = (it + 1) % 3;
@@ -995,7 +1001,7 @@ struct BfsRun {
         LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p + B_NEXT, 0, sizeof(int64_t), s));
         rep = 0;
       }
-      if (coop && nq <= COOP_MAX && mf <= COOP_EDGES) {
+      if (coop && nq >= COOP_MIN && nq <= COOP_MAX && mf <= COOP_EDGES) {
         // narrow levels on every SM: a cooperative launch (all CTAs resident), one grid barrier
         // per level, until the frontier widens past the cooperative limits or asks for a pull
         LAGR_CUDA_TRY(cudaMemsetAsync(cst.p, 0, sizeof(CoopState), s));
@@ -1022,7 +1028,7 @@ struct BfsRun {
         {
           KTimer kt(TK_BFS_SMALL, s);
           bfs_push_small<<<1, SMALL_THREADS, 0, s>>>(G->rowptr, G->colidx, qa.p, qb.p, visited.p, level, parent,
-                                                     cnt.p, n, push_only ? 0 : 1, hd);
+                                                     cnt.p, n, push_only ? 0 : 1, hd, coop ? COOP_MIN : SMALL_MAX);
         }
         LAGR_LAUNCH_CHECK();
         phase = 1;
