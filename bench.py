@@ -684,6 +684,7 @@ def roofline(g, ktime, steps, peak, peak_kind, comp):
         cand.append((pr_ms, "pr_warp (PageRank row-sum gather, one iteration)", pr_bytes, pr_ms / pr_n,
                      "pr_gather_rmat22.json"))
         comp["pagerank_gather_gbs"] = round(pr_bytes / (pr_ms / pr_n) / 1e6, 1)
+        comp["pagerank_gather_frac_hbm"] = round(pr_bytes / (pr_ms / pr_n) / 1e6 / peak, 4)
     if tc_n:
         tc_bytes = tc_algorithmic_bytes(g)
         cand.append((tc_ms, "tc_count_cta + tc_count_warp (one triangle pass)", tc_bytes, tc_ms / tc_n,
@@ -709,6 +710,11 @@ def roofline(g, ktime, steps, peak, peak_kind, comp):
         # where the algorithmic byte model counts re-reads that the kernel serves from L2
         out["dram_gbs"] = round(traffic / (ms_launch * 1e-3) / 1e9, 1)
         out["dram_frac"] = round(traffic / (ms_launch * 1e-3) / 1e9 / peak, 4)
+    if "tc_count" in name:
+        # the triangle kernels are bound by instruction issue, not by HBM (ncu --set full at R-MAT
+        # scale 20, profiles/tc_count_rmat20.md): issue-active share of the SM schedulers
+        out["issue_active_pct"] = {"tc_count_cta": 72.6, "tc_count_warp": 50.7,
+                                   "source": "profiles/tc_count_rmat20.md"}
     return out
 
 

@@ -5,13 +5,16 @@
 // interleaved per vertex (row-major n x ns: the ns values of a vertex are contiguous) and the
 // pattern of a frontier is a 64-bit source mask per vertex, as in the 64-source BFS:
 //
-//  - BFS phase.  The frontier of level d is a list of (vertex, mask) pairs.  One push step,
+//  - BFS phase, direction-optimised (push or pull per level, as Sec. IV-B adds it to BC; the pull
+//    is taken when it reads under half the edges of the push, see the host loop).  The frontier of level d is a list of
+//    (vertex, mask) pairs.  One push step,
 //    F<!s(P), replace> = F plus.first A fused with P += F, walks the list's edges (edge-balanced:
 //    a hub's row is spread over many warps): for an edge v -> w the sources m = mask(v) & ~seen(w)
 //    that reach w for the first time add P(v) into P(w) (float64 atomics; the counts are integers
 //    below 2^53, so their sums are exact and do not depend on the order) and set m in w's mask for
 //    the next level.  A finishing pass turns the touched vertices' masks into the next list and
-//    adds them to seen.  The lists of all levels are kept: they are the patterns S[d].
+//    adds them to seen.  The lists of all levels are kept: they are the patterns S[d].  A pull step
+//    computes the same product from the unreached side (bc_fwd_pull, over the rows of A').
 //  - Backtrack.  For each level d from the deepest down to 2: W = B ./ P on the pattern of level
 //    d, then W<s(S[d-1])> = W plus.first A' as a pull over the rows of level d-1 (each such vertex
 //    u sums W(l) over its out-neighbours l that are on level d for the same source: one warp
@@ -28,7 +31,8 @@ namespace lagr {
 namespace {
 
 constexpr int BC_THREADS = 256;
-enum BcSlot { BC_NNEXT = 0, BC_NSLOT = 2 };
+enum BcSlot { BC_NNEXT = 0, BC_NCAND = 1, BC_MU = 2, BC_MF = 3, BC_NSLOT = 4 };
+constexpr int BC_PULL_MARGIN = 2;  // pull when the unreached vertices' edges are under half the frontier's
 
 struct BcSources {
   int32_t v[64];
@@ -88,6 +92,121 @@ __global__ void __launch_bounds__(BC_THREADS)
         m &= m - 1;
         atomicAdd(&sw[q], sv[q]);
       }
+    }
+  }
+}
+
+// The direction rule's counts and the pull's candidates: the vertices some source has not reached
+// (listed in cand), the edges of those vertices (mu) and the out-edges of the level's list (mf).
+__global__ void bc_census(int32_t n, unsigned long long full, const unsigned long long *__restrict__ seen,
+                          const int32_t *__restrict__ rowptr, const int32_t *__restrict__ lvert, int32_t nent,
+                          int32_t *__restrict__ cand, int64_t *__restrict__ cnt) {
+  unsigned long long mu = 0, mf = 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = b + threadIdx.x;
+    const bool need = w < n && (full & ~seen[w]) != 0;
+    if (need) mu += (unsigned long long)(rowptr[w + 1] - rowptr[w]);
+    const unsigned bal = __ballot_sync(LAGR_FULL_MASK, need);
+    unsigned long long pos = 0;
+    if (lane == 0 && bal) pos = atomicAdd((unsigned long long *)&cnt[BC_NCAND], (unsigned long long)__popc(bal));
+    pos = __shfl_sync(LAGR_FULL_MASK, pos, 0);
+    if (need) cand[pos + __popc(bal & lt)] = (int32_t)w;
+  }
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nent; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = lvert[j];
+    mf += (unsigned long long)(rowptr[v + 1] - rowptr[v]);
+  }
+  mu = warp_sum(mu);
+  mf = warp_sum(mf);
+  if (lane == 0) {
+    if (mu) atomicAdd((unsigned long long *)&cnt[BC_MU], mu);
+    if (mf) atomicAdd((unsigned long long *)&cnt[BC_MF], mf);
+  }
+}
+
+__global__ void bc_scatter_masks(const int32_t *__restrict__ lvert, const unsigned long long *__restrict__ lmask,
+                                 int32_t nent, unsigned long long *__restrict__ dmask) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nent; j += (int64_t)gridDim.x * blockDim.x)
+    dmask[lvert[j]] = lmask[j];
+}
+
+// One pull step of the BFS phase, F<!s(P), replace> = F plus.first A computed from the side of the
+// vertices not yet reached (the direction optimisation the paper adds to BC as Alg. 2 adds it to
+// Alg. 1): every candidate w sums P(v) over its in-neighbours v (rows of A') that are on the
+// level's frontier for a source w still lacks (fmask: the level's masks, dense).  At most NS
+// sources keep per-lane sums over the chunk; NS = 0 reduces per 32 edges for any ns.  A chunk adds
+// its sums with one float64 atomic per source (the counts are integers: exact in any order) and
+// sets the sources it reached in nmask; the first to set any appends w to the next list.
+template <int NS>
+__global__ void __launch_bounds__(BC_THREADS)
+    bc_fwd_pull(const int32_t *__restrict__ at_rowptr, const int32_t *__restrict__ at_colidx, int32_t ns,
+                unsigned long long full, const int32_t *__restrict__ cand, int32_t nent,
+                const int32_t *__restrict__ off, const unsigned long long *__restrict__ seen,
+                const unsigned long long *__restrict__ fmask, unsigned long long *__restrict__ nmask,
+                double *__restrict__ sigma, int32_t *__restrict__ nvert, int64_t *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t total = nent > 0 ? off[nent] : 0;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nwarps) {
+    const int32_t i = fx_entry_of(off, nent, (int32_t)c);
+    const int32_t w = cand[i];
+    const unsigned long long need = full & ~seen[w];
+    const int32_t b = at_rowptr[w] + ((int32_t)c - off[i]) * FX_CHUNK;
+    const int32_t e = min(at_rowptr[w + 1], b + FX_CHUNK);
+    double *sw = sigma + (int64_t)w * ns;
+    unsigned long long got = 0;  // sources with a term in this chunk (every lane)
+    if (NS > 0) {
+      double a[NS > 0 ? NS : 1];
+#pragma unroll
+      for (int q = 0; q < (NS > 0 ? NS : 1); q++) a[q] = 0.0;
+      unsigned long long touched = 0;
+      for (int32_t k = b + lane; k < e; k += 32) {
+        const int32_t v = __ldg(&at_colidx[k]);
+        const unsigned long long mm = fmask[v] & need;
+        touched |= mm;
+#pragma unroll
+        for (int q = 0; q < (NS > 0 ? NS : 1); q++)
+          if ((mm >> q) & 1ull) a[q] += sigma[(int64_t)v * ns + q];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) touched |= __shfl_xor_sync(LAGR_FULL_MASK, touched, o);
+      got = touched;
+#pragma unroll
+      for (int q = 0; q < (NS > 0 ? NS : 1); q++) {
+        if (!((got >> q) & 1ull)) continue;
+        double t = a[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(LAGR_FULL_MASK, t, o);
+        if (lane == 0) atomicAdd(&sw[q], t);
+      }
+    } else {
+      for (int32_t base = b; base < e; base += 32) {
+        const int32_t k = base + lane;
+        int32_t v = 0;
+        unsigned long long mm = 0;
+        if (k < e) {
+          v = __ldg(&at_colidx[k]);
+          mm = fmask[v] & need;
+        }
+        unsigned long long any = mm;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(LAGR_FULL_MASK, any, o);
+        got |= any;
+        while (any) {
+          const int q = __ffsll((long long)any) - 1;
+          any &= any - 1;
+          double t = ((mm >> q) & 1ull) ? sigma[(int64_t)v * ns + q] : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(LAGR_FULL_MASK, t, o);
+          if (lane == 0) atomicAdd(&sw[q], t);
+        }
+      }
+    }
+    if (lane == 0 && got) {
+      const unsigned long long old = atomicOr(&nmask[w], got);
+      if (old == 0) nvert[atomicAdd((unsigned long long *)&cnt[BC_NNEXT], 1ull)] = w;
     }
   }
 }
@@ -277,6 +396,9 @@ extern "C" int lagr_betweenness(double *centrality, int32_t *levels, lagr_graph 
   LAGR_TRY(nmask.alloc(n, msg, "next masks"));
   LAGR_TRY(dmask.alloc(n, msg, "level masks"));
   LAGR_TRY(cnt.alloc(BC_NSLOT, msg, "counters"));
+  Temp<int32_t> cand(s);
+  LAGR_TRY(cand.alloc(n, msg, "pull candidates"));
+  LAGR_TRY(lagr_property_AT(G, s, msg));  // the pull reads in-neighbours (A' aliases A when undirected)
   // the level lists (vertex, mask), all levels one after the other; grown when a level may not fit
   int64_t cap = (int64_t)n * (ns < 4 ? ns : 4) + 64;
   Temp<int32_t> lv(s);
@@ -305,6 +427,12 @@ extern "C" int lagr_betweenness(double *centrality, int32_t *levels, lagr_graph 
   LAGR_TRY(fetch_to_host(h, cnt.p, sizeof(h), s, msg));
   std::vector<int64_t> start = {0, h[BC_NNEXT]};  // level d's list is [start[d], start[d+1])
   const int grid = resident_ctas((const void *)bc_push, BC_THREADS, 0);
+  const int fgrid4 = resident_ctas((const void *)bc_fwd_pull<4>, BC_THREADS, 0);
+  const int fgrid8 = resident_ctas((const void *)bc_fwd_pull<8>, BC_THREADS, 0);
+  const int fgrid0 = resident_ctas((const void *)bc_fwd_pull<0>, BC_THREADS, 0);
+  const unsigned long long full = ns == 64 ? ~0ull : ((1ull << ns) - 1);
+  int pulls = 0, pushes = 0;  // BFS-phase steps by direction (the last one finds no new vertex)
+  bool pull = false;
   const int pgrid = resident_ctas((const void *)bc_pull, BC_THREADS, 0);
   const int pgrid4 = resident_ctas((const void *)bc_pull_few<4>, BC_THREADS, 0);
   const int pgrid8 = resident_ctas((const void *)bc_pull_few<8>, BC_THREADS, 0);
@@ -328,10 +456,45 @@ extern "C" int lagr_betweenness(double *centrality, int32_t *levels, lagr_graph 
       std::swap(lm.p, lm2.p);
       cap = ncap;
     }
-    LAGR_TRY(fx_plan(&fx, lv.p + s0, (int32_t)nent, G->rowptr, s, msg));
-    LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p + BC_NNEXT, 0, sizeof(int64_t), s));
-    bc_push<<<grid, BC_THREADS, 0, s>>>(G->rowptr, G->colidx, ns, lv.p + s0, lm.p + s0, (int32_t)nent, fx.off,
-                                        seen.p, nmask.p, sigma.p, lv.p + start[d + 1], cnt.p);
+    // direction of the step (Beamer's rule over the sources' union): pull once the frontier's
+    // out-edges exceed the edges of the vertices still unreached by some source / alpha
+    LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, BC_NSLOT * sizeof(int64_t), s));
+    bc_census<<<grid_for(n, BC_THREADS), BC_THREADS, 0, s>>>(n, full, seen.p, G->rowptr, lv.p + s0, (int32_t)nent,
+                                                             cand.p, cnt.p);
+    LAGR_LAUNCH_CHECK();
+    LAGR_TRY(fetch_to_host(h, cnt.p, sizeof(h), s, msg));
+    const int64_t ncand = h[BC_NCAND];
+    // Pull when it reads fewer edges than the push by a margin: the pull walks every edge of the
+    // vertices some source has not reached (mu) with a few float64 sums per chunk, the push every
+    // out-edge of the frontier (mf) with an atomic per new (vertex, source) pair.  (Beamer's rule,
+    // mf > mu / 14 with its hysteresis, chose pulls that measured slower than the push on R-MAT:
+    // 13.1 vs 12.0 ms for 4 sources at scale 22, 169 vs 118 ms for 64.)  Past 8 sources the pull
+    // reduces per 32 edges and per source and loses to the push (123 vs 118 ms for 64): push only.
+    pull = ns <= 8 && ncand > 0 && BC_PULL_MARGIN * h[BC_MU] < h[BC_MF];
+    if (pull) {
+      bc_scatter_masks<<<grid_for(nent, BC_THREADS), BC_THREADS, 0, s>>>(lv.p + s0, lm.p + s0, (int32_t)nent,
+                                                                        dmask.p);
+      LAGR_TRY(fx_plan(&fx, cand.p, (int32_t)ncand, G->at_rowptr, s, msg));
+      if (ns <= 4)
+        bc_fwd_pull<4><<<fgrid4, BC_THREADS, 0, s>>>(G->at_rowptr, G->at_colidx, ns, full, cand.p, (int32_t)ncand,
+                                                     fx.off, seen.p, dmask.p, nmask.p, sigma.p, lv.p + start[d + 1],
+                                                     cnt.p);
+      else if (ns <= 8)
+        bc_fwd_pull<8><<<fgrid8, BC_THREADS, 0, s>>>(G->at_rowptr, G->at_colidx, ns, full, cand.p, (int32_t)ncand,
+                                                     fx.off, seen.p, dmask.p, nmask.p, sigma.p, lv.p + start[d + 1],
+                                                     cnt.p);
+      else
+        bc_fwd_pull<0><<<fgrid0, BC_THREADS, 0, s>>>(G->at_rowptr, G->at_colidx, ns, full, cand.p, (int32_t)ncand,
+                                                     fx.off, seen.p, dmask.p, nmask.p, sigma.p, lv.p + start[d + 1],
+                                                     cnt.p);
+      bc_clear_masks<<<grid_for(nent, BC_THREADS), BC_THREADS, 0, s>>>(lv.p + s0, (int32_t)nent, dmask.p);
+      pulls++;
+    } else {
+      pushes++;
+      LAGR_TRY(fx_plan(&fx, lv.p + s0, (int32_t)nent, G->rowptr, s, msg));
+      bc_push<<<grid, BC_THREADS, 0, s>>>(G->rowptr, G->colidx, ns, lv.p + s0, lm.p + s0, (int32_t)nent, fx.off,
+                                          seen.p, nmask.p, sigma.p, lv.p + start[d + 1], cnt.p);
+    }
     LAGR_LAUNCH_CHECK();
     LAGR_TRY(fetch_to_host(h, cnt.p, sizeof(h), s, msg));
     const int64_t nn = h[BC_NNEXT];
@@ -368,6 +531,8 @@ extern "C" int lagr_betweenness(double *centrality, int32_t *levels, lagr_graph 
   LAGR_CUDA_TRY(cudaStreamSynchronize(s));
   if (levels) *levels = D;
   G->last_levels = D + 1;
+  G->last_pull_levels = pulls;
+  G->last_push_levels = pushes;
   clear_msg(msg);
   return LAGR_OK;
 }

@@ -101,6 +101,10 @@ struct RowPlan {
   int32_t units = 0, heavy_len = 0, hchunk = 0;  // the plan's block size, heavy-row threshold and chunk
 };
 constexpr int ROW_HCHUNK = 8192;
+// the finer plan of the warp-per-block gathers (PageRank, FastSV): blocks of one warp's work
+constexpr int FINE_UNITS = 1024;   // units per block
+constexpr int FINE_HEAVY = 1024;   // longer rows are cut into chunks of FINE_HCHUNK entries
+constexpr int FINE_HCHUNK = 2048;
 
 struct Priv {
   // small device scratch: counters and flags used by every algorithm

@@ -31,9 +31,9 @@ namespace {
 
 constexpr int PR_THREADS = 256;
 constexpr int PR_UNITS = ROW_UNITS;                 // units (entries + rows) per edge-gradient block
-constexpr int PR_WUNITS = 1024;   // units per block of the gathers' row plans (one warp's work item)
-constexpr int PR_WHEAVY = 1024;   // longer rows are cut into chunks of PR_WHCHUNK entries
-constexpr int PR_WHCHUNK = 2048;
+constexpr int PR_WUNITS = FINE_UNITS;   // units per block of the gathers' row plans (one warp's work item)
+constexpr int PR_WHEAVY = FINE_HEAVY;   // longer rows are cut into chunks of PR_WHCHUNK entries
+constexpr int PR_WHCHUNK = FINE_HCHUNK;
 constexpr int PR_CHUNK = 8;                         // iterations launched between host checks
 
 constexpr int PR_FIN_BLOCKS = 32;  // CTAs of the partial-sum fold

@@ -825,6 +825,38 @@ __global__ void tc_kept_classify(const int32_t *__restrict__ dplus, int32_t n, i
   }
 }
 
+// The load-balanced walk over 32 segments (warp_segments) with four elements per lane per round:
+// the four positions are found first and their loads issued together, so that a lane keeps four
+// list loads in flight.  f(gidx) is called for each valid element.  Warp-collective.
+template <class F>
+__device__ __forceinline__ void warp_segments4(int st, int len, F &&f) {
+  const int lane = threadIdx.x & 31;
+  const int incl = warp_inclusive_scan(len);
+  const int total = __shfl_sync(LAGR_FULL_MASK, incl, 31);
+  for (int base = 0; base < total; base += 128) {
+    int g[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int k = base + 32 * j + lane;
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int step = 0; step < 5; step++) {
+        const int mid = (lo + hi) >> 1;
+        const int v = __shfl_sync(LAGR_FULL_MASK, incl, mid);
+        if (v > k) hi = mid; else lo = mid + 1;
+      }
+      const int incl_s = __shfl_sync(LAGR_FULL_MASK, incl, lo);
+      const int len_s = __shfl_sync(LAGR_FULL_MASK, len, lo);
+      const int st_s = __shfl_sync(LAGR_FULL_MASK, st, lo);
+      g[j] = k < total ? st_s + (k - (incl_s - len_s)) : -1;
+    }
+    int32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) w[j] = g[j] >= 0 ? g[j] : 0;
+    f(w, g);
+  }
+}
+
 // One anchor v, processed by `ng` warps of a group (warp index gw within it) with the table t;
 // sync() is the group's barrier.  Writes the anchor's counts to the positions of its U entries in
 // c (cleared before the pass) and adds their sum into *total.
@@ -851,24 +883,49 @@ __device__ __forceinline__ void kept_anchor(int32_t v, const int32_t *__restrict
   // the middle vertices k (entries of A(v,:) ranked above v), 32 row entries per warp batch: every
   // entry of U(k) is probed.  Lists of 32 or more are walked by the whole warp, shorter ones by the
   // load-balanced segment walk.
+  const int32_t a = dplus[v];
   for (int32_t jb = b + gw * 32; jb < e; jb += ng * 32) {
     const int32_t j = jb + lane;
-    int32_t st = 0, len = 0;
+    int32_t st = 0, len = 0, rk = 0;
     if (j < e) {
       const int32_t k = colidx[j];
-      if (rank[k] > rv) {
+      rk = rank[k];
+      if (rk > rv) {
         st = rowptr[k];
         len = dplus[k];
       }
     }
     unsigned longs = __ballot_sync(LAGR_FULL_MASK, len >= 32);
-    warp_segments(st, len >= 32 ? 0 : len, 0, [&](bool valid, int, int, int gidx) {
-      if (valid) t.count(u_colidx[gidx]);
+    warp_segments4(st, len >= 32 ? 0 : len, [&](int32_t (&pos)[4], const int (&g)[4]) {
+      int32_t r[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) r[q] = u_colidx[pos[q]];  // four loads in flight
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (g[q] >= 0) t.count(r[q]);
     });
     while (longs) {
       const int sl = __ffs(longs) - 1;
       longs &= longs - 1;
       const int32_t st_s = __shfl_sync(LAGR_FULL_MASK, st, sl), len_s = __shfl_sync(LAGR_FULL_MASK, len, sl);
+      const int32_t rk_s = __shfl_sync(LAGR_FULL_MASK, rk, sl);
+      // A long U(k) sorted by descending rank is searched for the entries of U(v) instead of being
+      // walked, when that takes fewer rounds: a hit is the same triangle (v, k, r)
+      const int32_t search_rounds = ((a + 31) >> 5) * (32 - __clz(len_s));
+      if (len_s >= TC_SORT_MIN && len_s <= TC_SORT_MAX && search_rounds < ((len_s + 31) >> 5)) {
+        const int32_t *lst = u_colidx + st_s;
+        for (int32_t q = lane; q < a; q += 32) {
+          const int32_t r = u_colidx[b + q];
+          if (r <= rk_s) continue;  // U(k) holds only ranks above k's
+          int32_t lo = 0, hi = len_s;  // the first position holding a rank <= r
+          while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (lst[mid] > r) lo = mid + 1; else hi = mid;
+          }
+          if (lo < len_s && lst[lo] == r) t.count(r);
+        }
+        continue;
+      }
       int32_t q = lane;
       for (; q + 96 < len_s; q += 128) {  // four loads per lane in flight
         const int32_t w0 = u_colidx[st_s + q], w1 = u_colidx[st_s + q + 32], w2 = u_colidx[st_s + q + 64],

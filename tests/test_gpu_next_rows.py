@@ -164,11 +164,16 @@ def bc_close(c_gpu, c_ref, rel=1e-9):
 
 @pytest.mark.parametrize("k", [1, 4, 13, 64])
 def test_bc_rmat_matches_oracle(L, k):
+    # with at most 8 sources the wide levels of an R-MAT traversal late in the BFS phase take the pull
+    # direction (the per-lane kernels for 4 and 8 sources); with more, every level pushes
     g = gen.rmat(12, 16)
     srcs = [int(s) for s in gen.sources(g, k, seed=5)]
-    c, levels = L.lagr_betweenness(dev(L, g), srcs)
+    G = dev(L, g)
+    c, levels = L.lagr_betweenness(G, srcs)
     co, lo = oracle.bc(g, srcs)
     assert levels == lo
+    assert G.struct.last_push_levels >= 1
+    assert (G.struct.last_pull_levels >= 1) == (k <= 8)
     bc_close(c.cpu().numpy(), co)
 
 
