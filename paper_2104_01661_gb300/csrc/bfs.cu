@@ -1006,7 +1006,7 @@ struct BfsRun {
         // per level, until the frontier widens past the cooperative limits or asks for a pull
         LAGR_CUDA_TRY(cudaMemsetAsync(cst.p, 0, sizeof(CoopState), s));
         const int res = resident_ctas((const void *)bfs_push_coop, COOP_THREADS, 0);
-        const int grid = res < 2 * sm_count() ? res : 2 * sm_count();
+        const int grid = res < sm_count() ? res : sm_count();  // 38 to 304 CTAs measured within 5 %
         const int32_t *rp = G->rowptr, *ci = G->colidx;
         int32_t *qap = qa.p, *qbp = qb.p, *lv = level, *pa = parent;
         uint32_t *vis = visited.p;

@@ -31,7 +31,12 @@ enum SpSlot {
   SP_NSLOT = 4
 };
 
-__device__ __forceinline__ long long bucket_of(float t, double delta) { return (long long)((double)t / delta); }
+// the bucket of a distance, floor(t / delta), as a float32 product with 1/delta (GB300's float64
+// division is slow, and the buckets only order the work: any monotone bucketing gives the same
+// distances, as long as every kernel uses the same one)
+__device__ __forceinline__ long long bucket_of(float t, float inv_delta) {
+  return (long long)fminf(t * inv_delta, 4.0e18f);  // (t >= 0 and finite here; clamped below 2^63)
+}
 
 __global__ void sp_init(int32_t n, int32_t src, int32_t *__restrict__ tbits, int32_t *__restrict__ qst,
                         int32_t *__restrict__ est, int32_t *__restrict__ q, int64_t *__restrict__ cnt) {
@@ -63,13 +68,12 @@ template <bool LIGHT>
 __global__ void __launch_bounds__(SP_THREADS)
     sp_relax(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const float *__restrict__ val,
              const int32_t *__restrict__ list, int32_t nent, const int32_t *__restrict__ off, float delta,
-             int32_t *__restrict__ tbits, long long cur, int32_t step, int32_t *__restrict__ qst,
+             float inv_delta, int32_t *__restrict__ tbits, long long cur, int32_t step, int32_t *__restrict__ qst,
              int32_t *__restrict__ qnext, int64_t *__restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int32_t total = nent > 0 ? off[nent] : 0;
-  const double ddelta = (double)delta;
-  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nwarps) {
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nwarps) {
     const int32_t i = fx_entry_of(off, nent, (int32_t)c);
     const int32_t u = list[i];
     const float tu = __int_as_float(__ldcg(&tbits[u]));
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(SP_THREADS)
       const int32_t cb = __float_as_int(cand);
       if (cb >= __ldcg(&tbits[v])) continue;  // a stale read only costs the atomic below
       const int32_t old = atomicMin(&tbits[v], cb);
-      if (LIGHT && cb < old && bucket_of(cand, ddelta) == cur && atomicExch(&qst[v], step) != step)
+      if (LIGHT && cb < old && bucket_of(cand, inv_delta) == cur && atomicExch(&qst[v], step) != step)
         qnext[atomicAdd((unsigned long long *)&cnt[SP_NQ], 1ull)] = v;
     }
   }
@@ -97,26 +101,26 @@ __global__ void sp_reset(int64_t *__restrict__ cnt) {
 }
 
 // the smallest distance beyond bucket `cur` (SP_TMIN holds +inf on entry)
-__global__ void sp_next_min(int32_t n, const int32_t *__restrict__ tbits, long long cur, float delta,
+__global__ void sp_next_min(int32_t n, const int32_t *__restrict__ tbits, long long cur, float inv_delta,
                             int64_t *__restrict__ cnt) {
   int32_t m = SP_INF_BITS;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t tb = tbits[i];
-    if (tb < SP_INF_BITS && tb < m && bucket_of(__int_as_float(tb), (double)delta) > cur) m = tb;
+    if (tb < SP_INF_BITS && tb < m && bucket_of(__int_as_float(tb), inv_delta) > cur) m = tb;
   }
   m = __reduce_min_sync(LAGR_FULL_MASK, m);
   if ((threadIdx.x & 31) == 0 && m < SP_INF_BITS) atomicMin((long long *)&cnt[SP_TMIN], (long long)m);
 }
 
 // the next bucket (that of the smallest distance beyond the current one) as the new frontier
-__global__ void sp_build(int32_t n, const int32_t *__restrict__ tbits, float delta, int32_t step,
+__global__ void sp_build(int32_t n, const int32_t *__restrict__ tbits, float inv_delta, int32_t step,
                          int32_t *__restrict__ qst, int32_t *__restrict__ q, int64_t *__restrict__ cnt) {
   const int64_t tmin = cnt[SP_TMIN];
   if (tmin >= SP_INF_BITS) return;
-  const long long nb = bucket_of(__int_as_float((int32_t)tmin), (double)delta);
+  const long long nb = bucket_of(__int_as_float((int32_t)tmin), inv_delta);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t tb = tbits[i];
-    if (tb < SP_INF_BITS && bucket_of(__int_as_float(tb), (double)delta) == nb) {
+    if (tb < SP_INF_BITS && bucket_of(__int_as_float(tb), inv_delta) == nb) {
       qst[i] = step;
       q[atomicAdd((unsigned long long *)&cnt[SP_NQ], 1ull)] = (int32_t)i;
     }
@@ -169,6 +173,8 @@ extern "C" int lagr_sssp(float *dist, int32_t *buckets, lagr_graph G, int32_t sr
   } fxg{&fx, s};
   LAGR_TRY(fx_alloc(&fx, n, s, msg));
   int32_t *tbits = reinterpret_cast<int32_t *>(dist);
+  const double invd = 1.0 / (double)delta;
+  const float inv_delta = invd < 3.0e38 ? (float)invd : 3.0e38f;  // finite for any positive delta
   const int relax_grid = resident_ctas((const void *)sp_relax<true>, SP_THREADS, 0);
   const int relax_grid_h = resident_ctas((const void *)sp_relax<false>, SP_THREADS, 0);
   sp_init<<<grid_for(n, SP_THREADS), SP_THREADS, 0, s>>>(n, src, tbits, qst.p, est.p, qa.p, cnt.p);
@@ -190,7 +196,7 @@ extern "C" int lagr_sssp(float *dist, int32_t *buckets, lagr_graph G, int32_t sr
       LAGR_TRY(fx_plan(&fx, q, (int32_t)nq, G->rowptr, s, msg));
       LAGR_CUDA_TRY(cudaMemsetAsync(cnt.p + SP_NQ, 0, sizeof(int64_t), s));
       sp_relax<true><<<relax_grid, SP_THREADS, 0, s>>>(G->rowptr, G->colidx, G->val, q, (int32_t)nq, fx.off, delta,
-                                                      tbits, cur, step, qst.p, qn, cnt.p);
+                                                      inv_delta, tbits, cur, step, qst.p, qn, cnt.p);
       LAGR_LAUNCH_CHECK();
       LAGR_TRY(fetch_to_host(h, cnt.p, sizeof(h), s, msg));
       nq = h[SP_NQ];
@@ -203,13 +209,13 @@ extern "C" int lagr_sssp(float *dist, int32_t *buckets, lagr_graph G, int32_t sr
     if (ne > 0) {
       LAGR_TRY(fx_plan(&fx, el.p, (int32_t)ne, G->rowptr, s, msg));
       sp_relax<false><<<relax_grid_h, SP_THREADS, 0, s>>>(G->rowptr, G->colidx, G->val, el.p, (int32_t)ne, fx.off,
-                                                         delta, tbits, cur, step, qst.p, qn, cnt.p);
+                                                         delta, inv_delta, tbits, cur, step, qst.p, qn, cnt.p);
     }
     // the next non-empty bucket becomes the frontier
     step++;
     sp_reset<<<1, 1, 0, s>>>(cnt.p);
-    sp_next_min<<<grid_for(n, SP_THREADS), SP_THREADS, 0, s>>>(n, tbits, cur, delta, cnt.p);
-    sp_build<<<grid_for(n, SP_THREADS), SP_THREADS, 0, s>>>(n, tbits, delta, step, qst.p, q, cnt.p);
+    sp_next_min<<<grid_for(n, SP_THREADS), SP_THREADS, 0, s>>>(n, tbits, cur, inv_delta, cnt.p);
+    sp_build<<<grid_for(n, SP_THREADS), SP_THREADS, 0, s>>>(n, tbits, inv_delta, step, qst.p, q, cnt.p);
     LAGR_LAUNCH_CHECK();
     LAGR_TRY(fetch_to_host(h, cnt.p, sizeof(h), s, msg));
     nq = h[SP_NQ];

@@ -777,9 +777,12 @@ struct KeptTable {
   int32_t *key, *pos;
   uint32_t *cnt;
   int logT;
-  bool global;  // the table is in global memory (reads bypass L1)
+  bool global;    // the table is in global memory (reads bypass L1)
+  uint32_t *bm;   // in shared memory: one bit per rank of [w0, n) held by the table (a filter)
+  int32_t w0;
   __device__ __forceinline__ int32_t rkey(int h) const { return global ? vload(&key[h]) : key[h]; }
   __device__ __forceinline__ void insert(int32_t r, int32_t p) const {
+    if (r >= w0) atomicOr(&bm[(r - w0) >> 5], 1u << ((r - w0) & 31));
     const uint32_t mask = (1u << logT) - 1;
     uint32_t h = hslot(r, logT);
     // at least twice as many slots as keys: a free slot exists; the bound only ends the loop
@@ -791,7 +794,10 @@ struct KeptTable {
       h = (h + 1) & mask;
     }
   }
+  // after the degree ordering most probes rank in the window, and most miss: one bitmap word
+  // settles them before the table
   __device__ __forceinline__ void count(int32_t r) const {
+    if (r >= w0 && !((bm[(r - w0) >> 5] >> ((r - w0) & 31)) & 1u)) return;
     const uint32_t mask = (1u << logT) - 1;
     uint32_t h = hslot(r, logT);
     for (uint32_t i = 0; i <= mask; i++) {
@@ -950,6 +956,10 @@ __device__ __forceinline__ void kept_anchor(int32_t v, const int32_t *__restrict
   }
   mine = warp_sum(mine);
   if (lane == 0 && mine) atomicAdd(total, mine);
+  for (int32_t q = gtid; q < a; q += gsize) {  // leave the filter clear for the next anchor
+    const int32_t r = u_colidx[b + q];
+    if (r >= t.w0) t.bm[(r - t.w0) >> 5] = 0u;
+  }
   sync();
 }
 
@@ -958,11 +968,14 @@ __global__ void __launch_bounds__(KEPT_WWARPS * 32)
     tc_kept_warp(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                  const int32_t *__restrict__ dplus, const int32_t *__restrict__ u_colidx,
                  const int32_t *__restrict__ rank, const int32_t *__restrict__ list, int64_t *__restrict__ ks,
-                 uint32_t *__restrict__ c) {
+                 uint32_t *__restrict__ c, int32_t w0w) {
   __shared__ int32_t skey[KEPT_WWARPS][KEPT_WSLOTS];
   __shared__ int32_t spos[KEPT_WWARPS][KEPT_WSLOTS];
   __shared__ uint32_t scnt[KEPT_WWARPS][KEPT_WSLOTS];
+  __shared__ uint32_t sbm[KEPT_WWARPS][(1 << TCW_WIN_LOG) / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = lane; i < (1 << TCW_WIN_LOG) / 32; i += 32) sbm[warp][i] = 0u;
+  __syncwarp();
   const int64_t nl = ks[KS_NW];
   for (;;) {
     long long it = 0;
@@ -970,7 +983,7 @@ __global__ void __launch_bounds__(KEPT_WWARPS * 32)
     it = __shfl_sync(LAGR_FULL_MASK, it, 0);
     if (it >= nl) break;
     const int32_t v = list[it];
-    const KeptTable t{skey[warp], spos[warp], scnt[warp], ceil_log2(2 * dplus[v]), false};
+    const KeptTable t{skey[warp], spos[warp], scnt[warp], ceil_log2(2 * dplus[v]), false, sbm[warp], w0w};
     kept_anchor(v, rowptr, colidx, dplus, u_colidx, rank, t, 0, 1, lane, 32, [] { __syncwarp(); }, c,
                 (unsigned long long *)&ks[KS_TOTAL]);
   }
@@ -983,9 +996,14 @@ __global__ void __launch_bounds__(KEPT_THREADS)
                 const int32_t *__restrict__ dplus, const int32_t *__restrict__ u_colidx,
                 const int32_t *__restrict__ rank, const int32_t *__restrict__ list, int64_t *__restrict__ ks,
                 int slot_n, int slot_q, int32_t *__restrict__ gkey, int32_t *__restrict__ gpos,
-                uint32_t *__restrict__ gcnt, const int32_t *__restrict__ hoff, uint32_t *__restrict__ c) {
+                uint32_t *__restrict__ gcnt, const int32_t *__restrict__ hoff, uint32_t *__restrict__ c,
+                int32_t w0c) {
   extern __shared__ int32_t ksm[];
   __shared__ long long s_it;
+  // the window filter: after the shared-memory table, or alone when the tables are global
+  uint32_t *bm = reinterpret_cast<uint32_t *>(gkey ? ksm : ksm + 3 * KEPT_SLOTS_MAX);
+  for (int i = threadIdx.x; i < (1 << TCC_WIN_LOG) / 32; i += blockDim.x) bm[i] = 0u;
+  __syncthreads();
   const int64_t nl = ks[slot_n];
   for (;;) {
     if (threadIdx.x == 0) s_it = (long long)atomicAdd((unsigned long long *)&ks[slot_q], 1ull);
@@ -997,6 +1015,8 @@ __global__ void __launch_bounds__(KEPT_THREADS)
     KeptTable t;
     t.logT = ceil_log2(2 * dplus[v]);
     t.global = gkey != nullptr;
+    t.bm = bm;
+    t.w0 = w0c;
     if (gkey) {
       t.key = gkey + hoff[it];
       t.pos = gpos + hoff[it];
@@ -1295,18 +1315,22 @@ extern "C" int lagr_tc_edges(uint32_t *c, uint64_t *ntriangles, lagr_graph G, in
     LAGR_TRY(gpos.alloc(tot, msg, "anchor positions"));
     LAGR_TRY(gcnt.alloc(tot, msg, "anchor counters"));
   }
-  const size_t csmem = (size_t)3 * KEPT_SLOTS_MAX * sizeof(int32_t);
+  const size_t bmbytes = ((size_t)1 << TCC_WIN_LOG) / 8;
+  const size_t csmem = (size_t)3 * KEPT_SLOTS_MAX * sizeof(int32_t) + bmbytes;
+  const int32_t w0c = n > (1 << TCC_WIN_LOG) ? n - (1 << TCC_WIN_LOG) : 0;
+  const int32_t w0w = n > (1 << TCW_WIN_LOG) ? n - (1 << TCW_WIN_LOG) : 0;
   LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_kept_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
   if (h[KS_NW] > 0)
     tc_kept_warp<<<resident_ctas((const void *)tc_kept_warp, KEPT_WWARPS * 32, 0), KEPT_WWARPS * 32, 0, s>>>(
-        G->rowptr, G->colidx, G->u_dplus, G->u_colidx, P->tc_rank, lw.p, ks.p, c);
+        G->rowptr, G->colidx, G->u_dplus, G->u_colidx, P->tc_rank, lw.p, ks.p, c, w0w);
   if (h[KS_NC] > 0)
     tc_kept_cta<<<resident_ctas((const void *)tc_kept_cta, KEPT_THREADS, csmem), KEPT_THREADS, csmem, s>>>(
         G->rowptr, G->colidx, G->u_dplus, G->u_colidx, P->tc_rank, lc.p, ks.p, KS_NC, KS_QC, nullptr, nullptr,
-        nullptr, nullptr, c);
+        nullptr, nullptr, c, w0c);
   if (nh > 0)
-    tc_kept_cta<<<sm_count(), KEPT_THREADS, 0, s>>>(G->rowptr, G->colidx, G->u_dplus, G->u_colidx, P->tc_rank,
-                                                    lh.p, ks.p, KS_NH, KS_QH, gkey.p, gpos.p, gcnt.p, hoff.p, c);
+    tc_kept_cta<<<sm_count(), KEPT_THREADS, bmbytes, s>>>(G->rowptr, G->colidx, G->u_dplus, G->u_colidx,
+                                                          P->tc_rank, lh.p, ks.p, KS_NH, KS_QH, gkey.p, gpos.p,
+                                                          gcnt.p, hoff.p, c, w0c);
   const int mg = resident_ctas((const void *)tc_kept_mirror, 256, 0);
   tc_kept_mirror<<<mg, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, rp.nblk, c, 0);
   tc_kept_mirror<<<mg, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, rp.nblk, c, 1);
