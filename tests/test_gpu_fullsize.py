@@ -166,3 +166,46 @@ def test_batch512_matches_plain_calls(L):
         ro, ito, _ = oracle.pagerank(parts[i], 0.85, 0.0, 20)
         assert ito == 20
         pr_close(rank[b.voff[i]:b.voff[i + 1]], ro)
+
+
+# ----------------------------------------------------------------------------------------------
+# the next rows at the sizes bench.py measures them (R-MAT 22 with pair weights; kept C at R-MAT 20,
+# whose oracle takes seconds, and at R-MAT 22 against the stored oracle count)
+# ----------------------------------------------------------------------------------------------
+
+def test_rmat22_fastsv_sssp_bc(L, rmat22):
+    g = gen.with_pair_weights(rmat22, seed=SEED)
+    G = L.Graph.from_host(g)
+    f, _ = L.lagr_connected_components(G)
+    fo, _ = oracle.fastsv(rmat22)
+    assert np.array_equal(f.cpu().numpy(), fo)
+    src = int(gen.sources(g, 1, seed=SEED)[0])
+    for delta in (0.1, 0.2):  # the deltas the bench tries
+        d, _ = L.lagr_sssp(G, src, delta)
+        assert np.array_equal(d.cpu().numpy(), oracle.sssp_delta(g, src, delta)[0])
+    srcs = [int(s) for s in gen.sources(g, 4, seed=SEED)]
+    c, levels = L.lagr_betweenness(G, srcs)
+    co, lo = oracle.bc(rmat22, srcs)
+    assert levels == lo
+    c = c.cpu().numpy()
+    assert np.abs(c - co).max() <= 1e-9 * max(np.abs(co).max(), 1.0)
+
+
+def test_kept_c_rmat19_and_rmat22(L, rmat22):
+    g = gen.rmat(19, 16, seed=SEED)
+    G = L.Graph.from_host(g)
+    c, t = L.lagr_tc_edges(G)
+    co, to = oracle.tc_edges(g)
+    assert t == to and np.array_equal(c.cpu().numpy().view(np.uint32), co)
+    G.free()
+    G22 = L.Graph.from_host(rmat22)
+    c22, t22 = L.lagr_tc_edges(G22)
+    assert t22 == golden22()["triangles"]
+    c22 = c22.cpu().numpy().view(np.uint32)
+    assert int(c22.sum(dtype=np.uint64)) == t22
+    # the U side of every edge holds 0; the L side of each triangle's first-last edge its count
+    deg = np.diff(rmat22.rowptr).astype(np.int64)
+    rank = np.empty(rmat22.n, dtype=np.int64)
+    rank[np.lexsort((np.arange(rmat22.n), deg))] = np.arange(rmat22.n)
+    rows = np.repeat(np.arange(rmat22.n, dtype=np.int64), deg)
+    assert (c22[rank[rows] < rank[rmat22.colidx]] == 0).all()
