@@ -183,7 +183,7 @@ def run_gpu(args):
     if args.only == "next":  # profiling case: the next rows alone on this graph (not a bench line)
         hbm_peak, _ = peaks()
         return {"config": {"workload": f"profiling case: rmat{args.scale}_ef{EF}, next rows (not a bench line)"},
-                "extras": extras_next_rows(L, dev, hbm_peak, g)} if rank == 0 else None
+                "extras": extras_next_rows(L, dev, hbm_peak, g, f"rmat{args.scale}")} if rank == 0 else None
     srcs = [int(s) for s in gen.sources(g, NSRC, seed=SEED)]
     n, nnz = g.n, g.nnz
     m_und = nnz // 2
@@ -393,7 +393,7 @@ def run_gpu(args):
             del rp, ci, level, parent
             torch.cuda.empty_cache()
             out["extras"] = extras(L, dev, hbm_peak)
-            out["extras"].update(extras_next_rows(L, dev, hbm_peak, g))
+            out["extras"].update(extras_next_rows(L, dev, hbm_peak, g, f"rmat{args.scale}"))
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -569,8 +569,8 @@ def extras(L, dev, hbm_peak):
     return res
 
 
-def extras_next_rows(L, dev, hbm_peak, g):
-    """The next rows on the bench graph (R-MAT 22): the kept C<s(L)> of Alg. 6 against the fused
+def extras_next_rows(L, dev, hbm_peak, g, tag):
+    """The next rows on the bench graph (R-MAT 22; `tag` names the graph in the keys): the kept C<s(L)> of Alg. 6 against the fused
     count, FastSV (Alg. 7), delta-stepping SSSP (Alg. 5) and batched betweenness centrality
     (Alg. 3), each with its algorithmic bytes and the fraction of HBM they reach."""
     import numpy as np
@@ -588,7 +588,7 @@ def extras_next_rows(L, dev, hbm_peak, g):
     fused_ms = _timed(lambda: L.lagr_tc(G))
     kept_ms = _timed(lambda: L.lagr_tc_edges(G, c=c))
     kb = tc_algorithmic_bytes(g) + 4 * nnz  # the fused pass's bytes plus the kept C written
-    res["tc_edges_rmat22"] = {"kept_ms": round(kept_ms, 3), "fused_count_ms": round(fused_ms, 3),
+    res[f"tc_edges_{tag}"] = {"kept_ms": round(kept_ms, 3), "fused_count_ms": round(fused_ms, 3),
                               "kept_over_fused": round(kept_ms / fused_ms, 2), "bytes": kb,
                               "gbs": round(kb / (kept_ms * 1e-3) / 1e9, 1),
                               "frac_hbm": round(kb / (kept_ms * 1e-3) / 1e9 / hbm_peak, 4)}
@@ -602,7 +602,7 @@ def extras_next_rows(L, dev, hbm_peak, g):
         rounds[0] = L.lagr_connected_components(G, component=comp)[1]
     cc_ms = _timed(cc)
     ccb = rounds[0] * (4 * (n + 1) + 4 * nnz + 44 * n)
-    res["fastsv_rmat22"] = {"ms": round(cc_ms, 3), "rounds": rounds[0], "components": int(torch.unique(comp).numel()),
+    res[f"fastsv_{tag}"] = {"ms": round(cc_ms, 3), "rounds": rounds[0], "components": int(torch.unique(comp).numel()),
                             "bytes": ccb, "gbs": round(ccb / (cc_ms * 1e-3) / 1e9, 1),
                             "frac_hbm": round(ccb / (cc_ms * 1e-3) / 1e9 / hbm_peak, 4)}
 
@@ -623,7 +623,7 @@ def extras_next_rows(L, dev, hbm_peak, g):
     reached = torch.isfinite(dist).cpu().numpy()
     comp_edges = int(deg[reached].sum()) // 2
     spb = 8 * int(deg[reached].sum()) + 4 * (n + 1) + 8 * n * best[2]
-    res["sssp_rmat22"] = {"ms": round(best[0], 3), "delta": best[1], "buckets": best[2],
+    res[f"sssp_{tag}"] = {"ms": round(best[0], 3), "delta": best[1], "buckets": best[2],
                           "gteps": round(comp_edges / (best[0] * 1e-3) / 1e9, 3), "bytes": spb,
                           "gbs": round(spb / (best[0] * 1e-3) / 1e9, 1),
                           "frac_hbm": round(spb / (best[0] * 1e-3) / 1e9 / hbm_peak, 4)}
@@ -639,7 +639,7 @@ def extras_next_rows(L, dev, hbm_peak, g):
         def bc():
             lv[0] = L.lagr_betweenness(G, srcs[:k], centrality=cent)[1]
         ms = _timed(bc, reps=1, warm=1)
-        res[f"bc{k}_rmat22"] = {"ms": round(ms, 3), "sources": k, "levels": lv[0],
+        res[f"bc{k}_{tag}"] = {"ms": round(ms, 3), "sources": k, "levels": lv[0],
                                 "mteps": round(k * (nnz // 2) / (ms * 1e-3) / 1e6, 1)}
     G.free()
     return res
