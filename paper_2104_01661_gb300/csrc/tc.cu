@@ -101,6 +101,12 @@ struct RankSet {
   __device__ __forceinline__ void erase(int32_t w) const {
     if (w >= w0) bm[(w - w0) >> 5] = 0u;
   }
+  // the anchor has no entries below the window (below == false): the bitmap decides alone, with
+  // no branch (ranks below w0 read word 0 and are masked off)
+  __device__ __forceinline__ uint32_t has_window(int32_t w) const {
+    const int32_t d = w - w0;
+    return (bm[max(d, 0) >> 5] >> (d & 31)) & (uint32_t)(d >= 0);
+  }
   __device__ __forceinline__ uint32_t has(int32_t w) const {
     const int32_t d = w - w0;
     // in the window the bitmap decides alone (it holds no rank <= rx); the word is read with a
@@ -157,13 +163,15 @@ __global__ void tc_rank_keys(const int32_t *__restrict__ rowptr, int32_t n, int3
   }
 }
 
-// rank[p[i]] = i after sorting, rank[v] = v when Alg. 6 does not sort
+// rank[p[i]] = i after sorting, rank[v] = v when Alg. 6 does not sort; rank[n + 1 + i] = the vertex
+// of rank i (rank has 2(n + 1) slots)
 __global__ void tc_rank_scatter(const int32_t *__restrict__ vals, int32_t n, const int64_t *__restrict__ dscal,
                                 int32_t *__restrict__ rank) {
   const int sort = (int)dscal[SL_SORT];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (sort) rank[vals[i]] = (int32_t)i;
-    else rank[i] = (int32_t)i;
+    const int32_t v = sort ? vals[i] : (int32_t)i;
+    rank[v] = (int32_t)i;
+    rank[n + 1 + i] = v;  // the vertex of rank i
   }
 }
 
@@ -455,14 +463,17 @@ __global__ void __launch_bounds__(TCS_CTA_THREADS)
 __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ dplus, int32_t n,
                             int32_t *__restrict__ listw, int2 *__restrict__ listwh, int64_t capwh,
                             int2 *__restrict__ listc, int64_t capc, int64_t *__restrict__ dscal, int wmax,
-                            int chunk) {
+                            int chunk, const int32_t *__restrict__ by_rank) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-    const int64_t v = base + lane;
+    // anchors in descending rank order: the CTA items of the top ranks first, whose walks read
+    // the top of the same lists, so that anchors in flight together share more of them in L2
+    const int64_t i = base + lane;
+    const int64_t v = i < n ? (int64_t)by_rank[n - 1 - i] : i;
     int32_t a = 0, dg = 0;
-    if (v < n) {
+    if (i < n) {
       a = dplus[v];
       dg = rowptr[v + 1] - rowptr[v];
     }
@@ -511,10 +522,60 @@ __global__ void tc_classify(const int32_t *__restrict__ rowptr, const int32_t *_
 
 // ---- intersection counts --------------------------------------------------------------------------
 
+// The next long list of a batch (lowest lane set in `longs`, which is cleared), with its first
+// four 32-entry groups loaded: entry base + lane of group q, or -1 past the end (-1 is in no set
+// and ranks at or below every anchor, so it ends a sorted walk and counts nothing).
+__device__ __forceinline__ const int32_t *next_long(unsigned &longs, int32_t st, int32_t len,
+                                                    const int32_t *__restrict__ u_colidx, int32_t &ls, int32_t &f0,
+                                                    int32_t &f1, int32_t &f2, int32_t &f3) {
+  const int lane = threadIdx.x & 31;
+  const int sl = __ffs(longs) - 1;
+  longs &= longs - 1;
+  const int32_t *lst = u_colidx + __shfl_sync(LAGR_FULL_MASK, st, sl);
+  ls = __shfl_sync(LAGR_FULL_MASK, len, sl);  // >= 32
+  f0 = lst[lane];
+  f1 = lane + 32 < ls ? lst[lane + 32] : -1;
+  f2 = lane + 64 < ls ? lst[lane + 64] : -1;
+  f3 = lane + 96 < ls ? lst[lane + 96] : -1;
+  return lst;
+}
+
+// One long list (32 entries or more) probed by the whole warp, its first block already loaded.  A
+// list sorted by descending rank ends its useful part at its first entry <= rx: the walk stops
+// after the first 32-entry group whose last entry is at or below rx.  Longer lists keep their
+// order and are walked to the end.
+template <class Probe>
+__device__ __forceinline__ uint32_t walk_long(const int32_t *__restrict__ lst, int32_t ls, int32_t rx, int32_t w0,
+                                              int32_t w1, int32_t w2, int32_t w3, Probe &&probe) {
+  const int lane = threadIdx.x & 31;
+  const bool sorted = ls >= TC_SORT_MIN && ls <= TC_SORT_MAX;
+  uint32_t c = 0;
+  for (int32_t base = 0;;) {  // warp-uniform: every lane runs every round
+    c += probe(w0);
+    if ((sorted && __shfl_sync(LAGR_FULL_MASK, w0, 31) <= rx) || base + 32 >= ls) break;
+    c += probe(w1);
+    if ((sorted && __shfl_sync(LAGR_FULL_MASK, w1, 31) <= rx) || base + 64 >= ls) break;
+    c += probe(w2);
+    if ((sorted && __shfl_sync(LAGR_FULL_MASK, w2, 31) <= rx) || base + 96 >= ls) break;
+    c += probe(w3);
+    if ((sorted && __shfl_sync(LAGR_FULL_MASK, w3, 31) <= rx) || base + 128 >= ls) break;
+    base += 128;
+    const int32_t k = base + lane;
+    w0 = k < ls ? lst[k] : -1;
+    w1 = k + 32 < ls ? lst[k + 32] : -1;
+    w2 = k + 64 < ls ? lst[k + 64] : -1;
+    w3 = k + 96 < ls ? lst[k + 96] : -1;
+  }
+  return c;
+}
+
 // One batch of (up to) 32 neighbours A(x, jb..min(jb+32,e)): for every neighbour y anchored at x
 // (smaller (d+, id)), probe each element of U(y,:) = u_colidx[ustart[y] .. ustart[y] + dplus[y])
-// against x's set.  Warp-collective.
-template <class Probe>
+// against x's set.  Warp-collective.  PIPE: the long lists are software-pipelined (the first block
+// of the next list is loaded while the current one is probed, and a list's first four groups come
+// in one round trip); otherwise each list is walked on its own, a load issued only while the walk
+// goes on (the CTA kernel: fewer registers, more resident warps).
+template <bool PIPE, class Probe>
 __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a, int32_t rx, int32_t jb, int32_t e,
                                                            const int32_t *__restrict__ colidx,
                                                            const int32_t *__restrict__ ustart,
@@ -536,57 +597,75 @@ __device__ __forceinline__ unsigned long long anchor_batch(int32_t x, int32_t a,
   // lengths are even enough (the longest at most twice the mean), each lane walks its own list;
   // otherwise the load-balanced walk spreads their elements over the lanes.
   unsigned longs = __ballot_sync(LAGR_FULL_MASK, len >= 32);
+  // PIPE: the first long list's first block is loaded before the short lists are walked
+  int32_t ls = 0, f0 = -1, f1 = -1, f2 = -1, f3 = -1;
+  const int32_t *lst = (PIPE && longs) ? next_long(longs, st, len, u_colidx, ls, f0, f1, f2, f3) : nullptr;
   const int32_t slen = len >= 32 ? 0 : len;
   const unsigned total = __reduce_add_sync(LAGR_FULL_MASK, (unsigned)slen);
   const unsigned lmax = __reduce_max_sync(LAGR_FULL_MASK, (unsigned)slen);
   if (32u * lmax <= 2u * total) {
-    const int32_t *lst = u_colidx + st;
+    const int32_t *own = u_colidx + st;
     int32_t q = 0;
     for (; q + 3 < slen; q += 4) {  // four independent loads in flight
-      const int32_t w0 = lst[q], w1 = lst[q + 1], w2 = lst[q + 2], w3 = lst[q + 3];
+      const int32_t w0 = own[q], w1 = own[q + 1], w2 = own[q + 2], w3 = own[q + 3];
       c += probe(w0) + probe(w1) + probe(w2) + probe(w3);
     }
-    for (; q < slen; q++) c += probe(lst[q]);
+    for (; q < slen; q++) c += probe(own[q]);
   } else if (total > 0) {
     warp_segments(st, slen, 0, [&](bool valid, int, int, int gidx) {
       if (valid) c += probe(u_colidx[gidx]);
     });
   }
-  while (longs) {
-    const int sl = __ffs(longs) - 1;
-    longs &= longs - 1;
-    const int32_t *lst = u_colidx + __shfl_sync(LAGR_FULL_MASK, st, sl);
-    const int32_t len_s = __shfl_sync(LAGR_FULL_MASK, len, sl);
-    // a sorted list (descending ranks) ends its useful part at its first entry <= rx
-    const bool sorted = len_s >= TC_SORT_MIN && len_s <= TC_SORT_MAX;
-    int32_t base = 0;  // warp-uniform: every lane runs every round
-    if (sorted) {
-      // four loads per lane in flight; the walk stops after the first 32-entry group whose last
-      // entry is at or below rx
-      for (; base + 128 <= len_s; base += 128) {
-        const int32_t k = base + lane;
-        const int32_t w0 = lst[k], w1 = lst[k + 32], w2 = lst[k + 64], w3 = lst[k + 96];
-        c += probe(w0);
-        if (__shfl_sync(LAGR_FULL_MASK, w0, 31) <= rx) { base = len_s; break; }
-        c += probe(w1);
-        if (__shfl_sync(LAGR_FULL_MASK, w1, 31) <= rx) { base = len_s; break; }
-        c += probe(w2);
-        if (__shfl_sync(LAGR_FULL_MASK, w2, 31) <= rx) { base = len_s; break; }
-        c += probe(w3);
-        if (__shfl_sync(LAGR_FULL_MASK, w3, 31) <= rx) { base = len_s; break; }
+  if (!PIPE) {
+    while (longs) {
+      const int sl = __ffs(longs) - 1;
+      longs &= longs - 1;
+      const int32_t *l = u_colidx + __shfl_sync(LAGR_FULL_MASK, st, sl);
+      const int32_t len_s = __shfl_sync(LAGR_FULL_MASK, len, sl);
+      // a sorted list (descending ranks) ends its useful part at its first entry <= rx
+      const bool sorted = len_s >= TC_SORT_MIN && len_s <= TC_SORT_MAX;
+      int32_t base = 0;  // warp-uniform: every lane runs every round
+      if (sorted) {
+        // four loads per lane in flight; the walk stops after the first 32-entry group whose last
+        // entry is at or below rx
+        for (; base + 128 <= len_s; base += 128) {
+          const int32_t k = base + lane;
+          const int32_t w0 = l[k], w1 = l[k + 32], w2 = l[k + 64], w3 = l[k + 96];
+          c += probe(w0);
+          if (__shfl_sync(LAGR_FULL_MASK, w0, 31) <= rx) { base = len_s; break; }
+          c += probe(w1);
+          if (__shfl_sync(LAGR_FULL_MASK, w1, 31) <= rx) { base = len_s; break; }
+          c += probe(w2);
+          if (__shfl_sync(LAGR_FULL_MASK, w2, 31) <= rx) { base = len_s; break; }
+          c += probe(w3);
+          if (__shfl_sync(LAGR_FULL_MASK, w3, 31) <= rx) { base = len_s; break; }
+        }
+      } else {
+        for (; base + 128 <= len_s; base += 128) {  // four loads per lane in flight
+          const int32_t k = base + lane;
+          const int32_t w0 = l[k], w1 = l[k + 32], w2 = l[k + 64], w3 = l[k + 96];
+          c += (probe(w0) + probe(w1)) + (probe(w2) + probe(w3));
+        }
       }
-    } else {
-      for (; base + 128 <= len_s; base += 128) {  // four loads per lane in flight
+      for (; base < len_s; base += 32) {
         const int32_t k = base + lane;
-        const int32_t w0 = lst[k], w1 = lst[k + 32], w2 = lst[k + 64], w3 = lst[k + 96];
-        c += (probe(w0) + probe(w1)) + (probe(w2) + probe(w3));
+        const int32_t w = k < len_s ? l[k] : 0;
+        if (k < len_s) c += probe(w);
+        if (sorted && __shfl_sync(LAGR_FULL_MASK, w, min(31, len_s - 1 - base)) <= rx) break;
       }
     }
-    for (; base < len_s; base += 32) {
-      const int32_t k = base + lane;
-      const int32_t w = k < len_s ? lst[k] : 0;
-      if (k < len_s) c += probe(w);
-      if (sorted && __shfl_sync(LAGR_FULL_MASK, w, min(31, len_s - 1 - base)) <= rx) break;
+  } else if (lst) {
+    for (;;) {
+      int32_t nls = 0, g0 = -1, g1 = -1, g2 = -1, g3 = -1;
+      const int32_t *nlst = longs ? next_long(longs, st, len, u_colidx, nls, g0, g1, g2, g3) : nullptr;
+      c += walk_long(lst, ls, rx, f0, f1, f2, f3, probe);
+      if (!nlst) break;
+      lst = nlst;
+      ls = nls;
+      f0 = g0;
+      f1 = g1;
+      f2 = g2;
+      f3 = g3;
     }
   }
   return c;
@@ -645,15 +724,28 @@ __global__ void __launch_bounds__(TCW_WARPS * 32, 4)
     // so it is valid whether or not entries fall below w0)
     const int32_t a = dplus[x];
     const int32_t ub = ustart[x];
-    const RankSet rs{bm, tab, ceil_log2(2 * a), w0, rank[x], nullptr, 0, false, true};
+    RankSet rs{bm, tab, ceil_log2(2 * a), w0, rank[x], nullptr, 0, false, true};
     const int T = 1 << rs.logT;
     for (int i = lane; i < T; i += 32) tab[i] = EMPTY;
     __syncwarp();
-    for (int i = lane; i < a; i += 32) rs.insert(u_colidx[ub + i]);
+    bool lb = false;  // entries below the window: without any, the bitmap decides alone
+    for (int i = lane; i < a; i += 32) {
+      const int32_t w = u_colidx[ub + i];
+      lb |= w < w0;
+      rs.insert(w);
+    }
+    rs.below = __any_sync(LAGR_FULL_MASK, lb);
     __syncwarp();
     unsigned long long c = 0;
-    for (int32_t jb = jb0; jb < je; jb += 32)
-      c += anchor_batch(x, a, rs.rx, jb, je, colidx, ustart, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
+    if (rs.below) {
+      for (int32_t jb = jb0; jb < je; jb += 32)
+        c += anchor_batch<true>(x, a, rs.rx, jb, je, colidx, ustart, u_colidx, dplus,
+                                [&](int32_t w) { return rs.has(w); });
+    } else {
+      for (int32_t jb = jb0; jb < je; jb += 32)
+        c += anchor_batch<true>(x, a, rs.rx, jb, je, colidx, ustart, u_colidx, dplus,
+                                [&](int32_t w) { return rs.has_window(w); });
+    }
     __syncwarp();
     for (int i = lane; i < a; i += 32) rs.erase(u_colidx[ub + i]);
     if (voff) {
@@ -726,7 +818,8 @@ __global__ void __launch_bounds__(TCC_THREADS)
       if (lane == 0) jb = atomicAdd(&s_next, 32);
       jb = __shfl_sync(LAGR_FULL_MASK, jb, 0);
       if (jb >= e) break;
-      c += anchor_batch(x, a, rs.rx, jb, e, colidx, ustart, u_colidx, dplus, [&](int32_t w) { return rs.has(w); });
+      c += anchor_batch<false>(x, a, rs.rx, jb, e, colidx, ustart, u_colidx, dplus,
+                               [&](int32_t w) { return rs.has(w); });
     }
     if (voff) {
       c = warp_sum(c);
@@ -1124,7 +1217,7 @@ int tc_alloc(lagr_graph G, Priv *P, TcParams prm, cudaStream_t s, char *msg) {
   LAGR_TRY(alloc_n(&P->tc_listwh, (size_t)capwh, s, msg, "warp anchor items"));
   P->tc_capwh = capwh;
   LAGR_TRY(alloc_n(&P->tc_listc, (size_t)capc, s, msg, "CTA anchors"));
-  LAGR_TRY(alloc_n(&P->tc_rank, (size_t)n + 1, s, msg, "degree ranks"));
+  LAGR_TRY(alloc_n(&P->tc_rank, 2 * ((size_t)n + 1), s, msg, "degree ranks and their order"));
   LAGR_TRY(alloc_n(&P->tc_sortbuf, 4 * (size_t)n + 4, s, msg, "rank sort buffers"));
   LAGR_TRY(alloc_n(&P->tc_radix, (size_t)radix_scratch_len(n), s, msg, "radix scratch"));
   LAGR_TRY(alloc_n(&P->tc_radix_scan, (size_t)scan_scratch_len(radix_scratch_len(n)), s, msg, "radix scan scratch"));
@@ -1175,7 +1268,7 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
     }
     tc_classify<<<grid_for(n, 256), 256, 0, s>>>(G->rowptr, G->u_dplus, n, P->tc_listw, P->tc_listwh,
                                                  P->tc_capwh, P->tc_listc, P->tc_capc, P->dscal, prm.wmax,
-                                                 prm.chunk);
+                                                 prm.chunk, P->tc_rank + n + 1);
     LAGR_LAUNCH_CHECK();
   } else {
     static_assert(SL_QC == SL_QW + 1 && SL_TOTAL == SL_QC + 1, "slot layout");
