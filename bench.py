@@ -711,10 +711,13 @@ def roofline(g, ktime, steps, peak, peak_kind, comp):
         out["dram_gbs"] = round(traffic / (ms_launch * 1e-3) / 1e9, 1)
         out["dram_frac"] = round(traffic / (ms_launch * 1e-3) / 1e9 / peak, 4)
     if "tc_count" in name:
-        # the triangle kernels are bound by instruction issue, not by HBM (ncu --set full at R-MAT
-        # scale 20, profiles/tc_count_rmat20.md): issue-active share of the SM schedulers
-        out["issue_active_pct"] = {"tc_count_cta": 72.6, "tc_count_warp": 50.7,
+        # the triangle kernels are bound by the latency of their dependent list walks, not by HBM
+        # bandwidth: issue-active share of the SM schedulers at R-MAT scale 20 (ncu --set full), and
+        # the L2 hit rate of the list reads at scale 22, where half of them go to DRAM
+        # (profiles/tc_count_rmat20.md)
+        out["issue_active_pct"] = {"tc_count_cta": 80.9, "tc_count_warp": 64.9,
                                    "source": "profiles/tc_count_rmat20.md"}
+        out["l2_hit_pct_rmat22"] = {"tc_count_cta": 51.5, "tc_count_warp": 47.0}
     return out
 
 
