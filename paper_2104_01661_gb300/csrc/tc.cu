@@ -17,6 +17,7 @@
 // probe is one shared-memory word, and an entry ranked below the anchor is rejected without any
 // lookup (it cannot be in the anchor's list).  Anchors with short lists run one per warp; long
 // lists or many neighbours run one CTA per (anchor, chunk of neighbours).
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 
@@ -187,11 +188,12 @@ constexpr int OR_SHORT = 32;
 
 __global__ void __launch_bounds__(256)
     tc_orient_rows(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                   const int32_t *__restrict__ rank, const int32_t *__restrict__ blk, int32_t *__restrict__ dplus,
-                   int32_t *__restrict__ u_colidx) {
+                   const int32_t *__restrict__ rank, const int32_t *__restrict__ blk,
+                   const uint8_t *__restrict__ hblk, int32_t *__restrict__ dplus, int32_t *__restrict__ u_colidx) {
   __shared__ int32_t stage[OR_STAGE];
   __shared__ int32_t longrows[ROW_UNITS / (OR_SHORT + 1) + 2];
   __shared__ int n_long;
+  if (hblk[blockIdx.x]) return;  // a heavy row alone: tc_orient_heavy orients it
   const int32_t r0 = blk[blockIdx.x], r1 = blk[blockIdx.x + 1];
   const int32_t e0 = rowptr[r0], e1 = rowptr[r1];
   const bool staged = e1 - e0 <= OR_STAGE;
@@ -199,15 +201,12 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) n_long = 0;
   if (staged) {
     int32_t k = e0 + threadIdx.x;
-    for (; k + 3 * 256 < e1; k += 4 * 256) {
-      const int32_t d0 = __ldg(&rank[colidx[k]]);
-      const int32_t d1 = __ldg(&rank[colidx[k + 256]]);
-      const int32_t d2 = __ldg(&rank[colidx[k + 512]]);
-      const int32_t d3 = __ldg(&rank[colidx[k + 768]]);
-      stage[k - e0] = d0;
-      stage[k + 256 - e0] = d1;
-      stage[k + 512 - e0] = d2;
-      stage[k + 768 - e0] = d3;
+    for (; k + 7 * 256 < e1; k += 8 * 256) {  // eight gathers per thread in flight
+      int32_t d[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) d[i] = __ldg(&rank[colidx[k + i * 256]]);
+#pragma unroll
+      for (int i = 0; i < 8; i++) stage[k + i * 256 - e0] = d[i];
     }
     for (; k < e1; k += 256) stage[k - e0] = __ldg(&rank[colidx[k]]);
   }
@@ -249,38 +248,56 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// the rows longer than ROW_HEAVY: one CTA each, the same output as tc_orient_rows
-__global__ void tc_orient_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                const int32_t *__restrict__ rank, int32_t *__restrict__ dplus,
-                                int32_t *__restrict__ u_colidx, const int32_t *__restrict__ heavy, int32_t nh) {
-  __shared__ int wc[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// The rows longer than ROW_HEAVY, in the row plan's chunks of ROW_HCHUNK entries, a CTA per chunk,
+// so that a hub row is spread over many SMs: each warp gathers the ranks of 256 entries at a time
+// (eight per lane in flight), compacts those above rank(v) with ballots and reserves their slots
+// of U(v) with one atomic on d+(v) (zeroed first by tc_orient_heavy_zero).  U(v) then keeps A's
+// order within each warp's run but not between runs, which nothing relies on: the U rows of 32 to
+// 16384 entries are sorted afterwards, and the other lists are walked or probed whole.
+constexpr int OH_THREADS = 256;
+constexpr int OH_PER = 8;  // entries per lane per round
+
+__global__ void tc_orient_heavy_zero(const int32_t *__restrict__ heavy, int32_t nh, int32_t *__restrict__ dplus) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x)
+    dplus[heavy[h]] = 0;
+}
+
+__global__ void __launch_bounds__(OH_THREADS)
+    tc_orient_heavy(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                    const int32_t *__restrict__ rank, int32_t *__restrict__ dplus, int32_t *__restrict__ u_colidx,
+                    const int32_t *__restrict__ heavy, const int32_t *__restrict__ hc_off,
+                    const int32_t *__restrict__ hc_row, int32_t nhc, int32_t hchunk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
-  for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
+  for (int64_t c = blockIdx.x; c < nhc; c += gridDim.x) {
+    const int32_t h = hc_row[c];
     const int32_t v = heavy[h];
-    const int32_t b = rowptr[v], e = rowptr[v + 1], rv = rank[v];
-    int32_t out = b;
-    for (int32_t base = b; base < e; base += blockDim.x) {
-      const int32_t k = base + threadIdx.x;
-      int32_t u = 0;
-      bool f = false;
-      if (k < e) {
-        u = __ldg(&rank[colidx[k]]);
-        f = u > rv;
+    const int32_t rv = rank[v], row0 = rowptr[v];
+    const int32_t b = row0 + (int32_t)(c - hc_off[h]) * hchunk;
+    const int32_t e = min(rowptr[v + 1], b + hchunk);
+    for (int32_t base = b + warp * 32 * OH_PER; base < e; base += OH_THREADS * OH_PER) {
+      int32_t u[OH_PER];
+      unsigned bal[OH_PER];
+      int tot = 0;
+#pragma unroll
+      for (int i = 0; i < OH_PER; i++) {
+        const int32_t k = base + i * 32 + lane;
+        u[i] = k < e ? __ldg(&rank[colidx[k]]) : -1;
       }
-      const unsigned bal = __ballot_sync(LAGR_FULL_MASK, f);
-      if (lane == 0) wc[warp] = __popc(bal);
-      __syncthreads();
-      int before = 0, total = 0;
-      for (int w = 0; w < nwarps; w++) {
-        if (w < warp) before += wc[w];
-        total += wc[w];
+#pragma unroll
+      for (int i = 0; i < OH_PER; i++) {
+        bal[i] = __ballot_sync(LAGR_FULL_MASK, u[i] > rv);
+        tot += __popc(bal[i]);
       }
-      if (f) u_colidx[out + before + __popc(bal & lt)] = u;
-      __syncthreads();
-      out += total;
+      int32_t out = 0;
+      if (lane == 0 && tot) out = atomicAdd(&dplus[v], tot);
+      out = row0 + __shfl_sync(LAGR_FULL_MASK, out, 0);
+#pragma unroll
+      for (int i = 0; i < OH_PER; i++) {
+        if (u[i] > rv) u_colidx[out + __popc(bal[i] & lt)] = u[i];
+        out += __popc(bal[i]);
+      }
     }
-    if (threadIdx.x == 0) dplus[v] = out - b;
   }
 }
 
@@ -1252,10 +1269,14 @@ int tc_launch(lagr_graph G, Priv *P, int method, TcParams prm, const int32_t *vo
     LAGR_TRY(radix_sort_pairs(keys, vals, tk, tv, n, bits, s, msg, P->tc_radix, P->tc_radix_scan));
     tc_rank_scatter<<<grid_for(n, 256), 256, 0, s>>>(vals, n, P->dscal, P->tc_rank);
     const RowPlan &rp = P->pr_at;
-    tc_orient_rows<<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, G->u_dplus, G->u_colidx);
     if (rp.nheavy > 0)
-      tc_orient_heavy<<<2 * sm_count(), 512, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, G->u_dplus, G->u_colidx, rp.heavy,
-                                              rp.nheavy);
+      tc_orient_heavy_zero<<<grid_for(rp.nheavy, 256), 256, 0, s>>>(rp.heavy, rp.nheavy, G->u_dplus);
+    tc_orient_rows<<<rp.nblk, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, rp.hblk, G->u_dplus,
+                                           G->u_colidx);
+    if (rp.nhc > 0)
+      tc_orient_heavy<<<std::min(rp.nhc, resident_ctas((const void *)tc_orient_heavy, OH_THREADS, 0)), OH_THREADS, 0,
+                        s>>>(G->rowptr, G->colidx, P->tc_rank, G->u_dplus, G->u_colidx, rp.heavy, rp.hc_off,
+                             rp.hc_row, rp.nhc, rp.hchunk);
     {  // the rows to sort are listed in the rank-sort buffers (4n ints, free again once the ranks
        // are made): n pairs for the short rows, then n shared by the CTA rows and the long ones
       int2 *lw = reinterpret_cast<int2 *>(P->tc_sortbuf), *lc = lw + n, *lm_end = lw + 2 * (int64_t)n;
