@@ -1042,16 +1042,18 @@ __device__ __forceinline__ void kept_anchor(int32_t v, const int32_t *__restrict
         }
         continue;
       }
-      int32_t q = lane;
-      for (; q + 96 < len_s; q += 128) {  // four loads per lane in flight
-        const int32_t w0 = u_colidx[st_s + q], w1 = u_colidx[st_s + q + 32], w2 = u_colidx[st_s + q + 64],
-                      w3 = u_colidx[st_s + q + 96];
+      // four groups per round trip, the last round's loads masked at the list's end (every entry is
+      // probed, so no load is wasted and a list of 32 to 128 entries costs one round trip)
+      for (int32_t q = lane; q < len_s; q += 128) {
+        const int32_t w0 = u_colidx[st_s + q];
+        const int32_t w1 = q + 32 < len_s ? u_colidx[st_s + q + 32] : -1;
+        const int32_t w2 = q + 64 < len_s ? u_colidx[st_s + q + 64] : -1;
+        const int32_t w3 = q + 96 < len_s ? u_colidx[st_s + q + 96] : -1;
         t.count(w0);
-        t.count(w1);
-        t.count(w2);
-        t.count(w3);
+        if (w1 >= 0) t.count(w1);
+        if (w2 >= 0) t.count(w2);
+        if (w3 >= 0) t.count(w3);
       }
-      for (; q < len_s; q += 32) t.count(u_colidx[st_s + q]);
     }
   }
   sync();
