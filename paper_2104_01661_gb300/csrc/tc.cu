@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(TCC_THREADS)
 // against it, and a hit on key i counts one triangle (j, k, i) for C(i, j).  The anchor then writes
 // its counts to the positions of its own entries (j, i) -- the U side; a second pass moves each
 // value to the mirror entry (i, j) on the L side (found by binary search in the lower vertex's
-// row j, short after the degree ordering) and clears the U side.  Every anchor owns its table, so
+// row j, short after the degree ordering) and clears the U entry it read.  Every anchor owns its table, so
 // the counts are exact; their sum is t.  Anchors with d+ <= 256 run one per warp (a 512-slot
 // table in shared memory), those up to KEPT_CTA_MAXD one per CTA (the table in shared memory),
 // longer ones one per CTA with the table in global memory.
@@ -1143,11 +1143,11 @@ __global__ void __launch_bounds__(KEPT_THREADS)
   }
 }
 
-// The counts sit at the U side (v, i); move each to the mirror entry (i, v) of L.  One thread per
-// entry of L: the mirror is in the row of the lower vertex.  A second pass clears the U side.
+// The counts sit at the U side (v, i); move each to the mirror entry (i, v) of L and clear it.  One
+// thread per entry of L: the mirror is in the row of the lower vertex.
 __global__ void tc_kept_mirror(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                                const int32_t *__restrict__ rank, const int32_t *__restrict__ blk, int32_t nblk,
-                               uint32_t *__restrict__ c, int clear) {
+                               uint32_t *__restrict__ c) {
   // one CTA per row block of the plan; entries walked in order, rows found in staged pointers
   __shared__ int32_t rp[ROW_UNITS + 1];
   for (int32_t bb = blockIdx.x; bb < nblk; bb += gridDim.x) {
@@ -1164,18 +1164,19 @@ __global__ void tc_kept_mirror(const int32_t *__restrict__ rowptr, const int32_t
         if (rp[mid] <= k) lo = mid; else hi = mid - 1;
       }
       const int32_t i = r0 + lo, j = colidx[k];
-      const bool in_l = rank[i] > rank[j];
-      if (clear) {
-        if (!in_l) c[k] = 0u;
-        continue;
-      }
-      if (!in_l) continue;
+      if (rank[i] <= rank[j]) continue;  // a U-side entry: cleared by the thread of its mirror
       int32_t a = rowptr[j], z = rowptr[j + 1];  // (j, i) in row j
       while (a < z) {
         const int32_t mid = a + ((z - a) >> 1);
         if (colidx[mid] < i) a = mid + 1; else z = mid;
       }
-      c[k] = (a < rowptr[j + 1] && colidx[a] == i) ? c[a] : 0u;
+      if (a < rowptr[j + 1] && colidx[a] == i) {
+        // the U-side entry (j, i) is the mirror of this entry only, so this thread alone reads and
+        // clears it; no thread reads an L-side entry
+        const uint32_t v = c[a];
+        c[k] = v;
+        if (v) c[a] = 0u;
+      }
     }
   }
 }
@@ -1448,8 +1449,7 @@ extern "C" int lagr_tc_edges(uint32_t *c, uint64_t *ntriangles, lagr_graph G, in
                                                           P->tc_rank, lh.p, ks.p, KS_NH, KS_QH, gkey.p, gpos.p,
                                                           gcnt.p, hoff.p, c, w0c);
   const int mg = resident_ctas((const void *)tc_kept_mirror, 256, 0);
-  tc_kept_mirror<<<mg, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, rp.nblk, c, 0);
-  tc_kept_mirror<<<mg, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, rp.nblk, c, 1);
+  tc_kept_mirror<<<mg, 256, 0, s>>>(G->rowptr, G->colidx, P->tc_rank, rp.blk, rp.nblk, c);
   LAGR_LAUNCH_CHECK();
   LAGR_TRY(fetch_to_host(h, ks.p, sizeof(h), s, msg));
   if (ntriangles) *ntriangles = (uint64_t)h[KS_TOTAL];
