@@ -274,10 +274,10 @@ def run_gpu(args):
     # streams, one for uploads and one for downloads, pipelined with the compute: uploads run up to
     # PIPE_DEPTH - 1 steps ahead and each step's results are downloaded while later steps compute
     # (inputs and outputs held in PIPE_DEPTH device buffers each, so the timed loop allocates
-    # nothing).  The depth absorbs the windows of slow host copies seen on the GB300 hosts (after a
-    # long GPU test run, copies that take 2.5-2.9 ms took 34-70 ms for about a tenth of a second),
-    # and the pipeline runs at least three untimed steps first (start-up, not the steady state the
-    # metric describes).  The timed region still holds every step's copies: it opens before the
+    # nothing).  The depth absorbs windows of slow host copies (measured right after another process
+    # had used the GPU heavily: copies that take 2.5-2.9 ms took 34-70 ms for about a tenth of a
+    # second), and the pipeline runs at least three untimed steps first (start-up, not the steady
+    # state the metric describes).  The timed region still holds every step's copies: it opens before the
     # first upload and closes after the last download.
     h2d = rp_h.numel() * 4 + ci_h.numel() * 4
     d2h = sum(t.numel() * 4 for t in hosts[0]) + 8
