@@ -872,6 +872,7 @@ constexpr int KEPT_WSLOTS = 512;
 constexpr int KEPT_WMAXD = KEPT_WSLOTS / 2;
 constexpr int KEPT_CTA_MAXD = 4096;
 constexpr int KEPT_THREADS = 256;
+constexpr int KEPT_WIN_LOG = 13;  // warp anchors' window filter: the top 8192 ranks (1 KB of bits)
 constexpr int KEPT_WWARPS = 4;                     // warps per CTA of the warp-anchor kernel
 constexpr int KEPT_SLOTS_MAX = 2 * KEPT_CTA_MAXD;  // table slots of the largest shared-memory table
 enum KeptSlot { KS_NW = 0, KS_NC = 1, KS_NH = 2, KS_QW = 3, KS_QC = 4, KS_QH = 5, KS_TOTAL = 6, KS_NSLOT = 8 };
@@ -1084,9 +1085,9 @@ __global__ void __launch_bounds__(KEPT_WWARPS * 32)
   __shared__ int32_t skey[KEPT_WWARPS][KEPT_WSLOTS];
   __shared__ int32_t spos[KEPT_WWARPS][KEPT_WSLOTS];
   __shared__ uint32_t scnt[KEPT_WWARPS][KEPT_WSLOTS];
-  __shared__ uint32_t sbm[KEPT_WWARPS][(1 << TCW_WIN_LOG) / 32];
+  __shared__ uint32_t sbm[KEPT_WWARPS][(1 << KEPT_WIN_LOG) / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = lane; i < (1 << TCW_WIN_LOG) / 32; i += 32) sbm[warp][i] = 0u;
+  for (int i = lane; i < (1 << KEPT_WIN_LOG) / 32; i += 32) sbm[warp][i] = 0u;
   __syncwarp();
   const int64_t nl = ks[KS_NW];
   for (;;) {
@@ -1435,7 +1436,7 @@ extern "C" int lagr_tc_edges(uint32_t *c, uint64_t *ntriangles, lagr_graph G, in
   const size_t bmbytes = ((size_t)1 << TCC_WIN_LOG) / 8;
   const size_t csmem = (size_t)3 * KEPT_SLOTS_MAX * sizeof(int32_t) + bmbytes;
   const int32_t w0c = n > (1 << TCC_WIN_LOG) ? n - (1 << TCC_WIN_LOG) : 0;
-  const int32_t w0w = n > (1 << TCW_WIN_LOG) ? n - (1 << TCW_WIN_LOG) : 0;
+  const int32_t w0w = n > (1 << KEPT_WIN_LOG) ? n - (1 << KEPT_WIN_LOG) : 0;
   LAGR_CUDA_TRY(cudaFuncSetAttribute(tc_kept_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
   if (h[KS_NW] > 0)
     tc_kept_warp<<<resident_ctas((const void *)tc_kept_warp, KEPT_WWARPS * 32, 0), KEPT_WWARPS * 32, 0, s>>>(
