@@ -79,16 +79,31 @@ __global__ void __launch_bounds__(SP_THREADS)
     const float tu = __int_as_float(__ldcg(&tbits[u]));
     const int32_t b = rowptr[u] + ((int32_t)c - off[i]) * FX_CHUNK;
     const int32_t e = min(rowptr[u + 1], b + FX_CHUNK);
-    for (int32_t k = b + lane; k < e; k += 32) {
-      const float w = __ldg(&val[k]);
-      if (LIGHT ? !(w > 0.0f && w <= delta) : !(w > delta)) continue;
-      const int32_t v = __ldg(&colidx[k]);
-      const float cand = __fadd_rn(tu, w);
+    // the chunk's (up to) four steps of 32 edges: weights and targets loaded first, then the
+    // targets' distances, so that each kind of load has four in flight per lane
+    constexpr int STEPS = FX_CHUNK / 32;
+    float w[STEPS];
+    int32_t v[STEPS], tv[STEPS];
+#pragma unroll
+    for (int q = 0; q < STEPS; q++) {
+      const int32_t k = b + lane + 32 * q;
+      w[q] = k < e ? __ldg(&val[k]) : -1.0f;  // -1: in neither class
+      v[q] = k < e ? __ldg(&colidx[k]) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < STEPS; q++) {
+      const bool in = LIGHT ? (w[q] > 0.0f && w[q] <= delta) : (w[q] > delta);
+      tv[q] = in ? __ldcg(&tbits[v[q]]) : INT32_MIN;  // INT32_MIN: nothing to relax
+    }
+#pragma unroll
+    for (int q = 0; q < STEPS; q++) {
+      if (tv[q] == INT32_MIN) continue;
+      const float cand = __fadd_rn(tu, w[q]);
       const int32_t cb = __float_as_int(cand);
-      if (cb >= __ldcg(&tbits[v])) continue;  // a stale read only costs the atomic below
-      const int32_t old = atomicMin(&tbits[v], cb);
-      if (LIGHT && cb < old && bucket_of(cand, inv_delta) == cur && atomicExch(&qst[v], step) != step)
-        qnext[atomicAdd((unsigned long long *)&cnt[SP_NQ], 1ull)] = v;
+      if (cb >= tv[q]) continue;  // a stale read only costs the atomic below
+      const int32_t old = atomicMin(&tbits[v[q]], cb);
+      if (LIGHT && cb < old && bucket_of(cand, inv_delta) == cur && atomicExch(&qst[v[q]], step) != step)
+        qnext[atomicAdd((unsigned long long *)&cnt[SP_NQ], 1ull)] = v[q];
     }
   }
 }
